@@ -1,0 +1,197 @@
+/*
+ * slipspring.h -- C ABI of the GB300 (sm_103a) library for the single-chain
+ * slip-spring model of T. Uneyama, arXiv:1106.2899.
+ *
+ * The library advances many independent chains.  Each chain has N beads R_i
+ * (Sec. 2.1), Z slip-springs with bead index S_j and anchor A_j (Sec. 2.1,
+ * Z <= z_max <= N, the paper's bound for one slot per bead, Sec. 3.2), and is
+ * stepped by the three substeps of Sec. 3.1: Euler-Maruyama beads with
+ * affinely advected anchors (Eqs. langevin_equation_bead_position,
+ * dynamic_equation_anchoring_position), capped Glauber hops (Eqs.
+ * transition_probability_s_plus/minus), creation and destruction at the chain
+ * ends (Eqs. transition_probability_z_plus/minus).  After every step the
+ * library samples the stress (Eq. stress_tensor_single_chain) and the virtual
+ * stress (App. B) into a multiple-tau correlator for G(t) (Eq.
+ * relaxation_modulus_tensor_green_kubo_form) and, every log_every steps, into
+ * ensemble sums for <sigma>(t) and eta+(t) (Sec. 4.1).
+ *
+ * Conventions
+ *  - Every function returns an int status: SS_OK (0) or a negative SS_E* code;
+ *    ss_last_error() gives a message for the last failure on that context.
+ *  - Units: b, kT and zeta as given in ss_params (the paper uses b = kT =
+ *    zeta = 1, Sec. 3.1).  Stresses in kT per chain; G in rho0 kT (the
+ *    per-chain correlation divided by N kT^2, c0 = rho0/N); time in units of
+ *    the time step times dt.
+ *  - Bead indices are 0-based (bead 0 = the paper's bead 1).
+ *  - Host arrays are caller-owned, C-contiguous, and only read or written
+ *    during the call.  The library owns every device allocation it makes.
+ *  - Calls enqueue work on the context's CUDA stream and return; the calls
+ *    that write host arrays synchronise that stream first.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef SLIPSPRING_H
+#define SLIPSPRING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SS_OK 0
+#define SS_EINVAL (-1)     /* invalid argument or parameter                        */
+#define SS_ENOMEM (-2)     /* device or host allocation failed                     */
+#define SS_ECUDA (-3)      /* a CUDA runtime call failed                           */
+#define SS_EOVERFLOW (-4)  /* non-finite state, or the step counter would wrap 2^32 */
+#define SS_ESTATE (-5)     /* call out of order (e.g. ss_run before ss_set_params)  */
+#define SS_ETIMEOUT (-6)   /* reserved: a bounded device wait gave up              */
+
+/* precisions */
+#define SS_FP32 0 /* FP32 beads and anchors, FP64 ensemble sums */
+#define SS_FP64 1 /* FP64 throughout                            */
+
+/* correlator channels (Eq. relaxation_modulus_tensor_green_kubo_form) */
+#define SS_CH_AUTO 0  /* (1/N) <sigma_ab(t) sigma_ab(0)>                 */
+#define SS_CH_CROSS 1 /* (1/N) <sigma_ab(t) sigma^(v)_ab(0)>             */
+#define SS_CH_TOTAL 2 /* AUTO + CROSS: the paper's G(t)                   */
+
+#define SS_CORR_POINTS 16 /* multiple-tau points per level */
+#define SS_MAX_LEVELS 32
+#define SS_MAX_BEADS 32   /* chain length limit of this build             */
+
+typedef struct ss_ctx ss_ctx;
+
+/* One ensemble ("element") of independent chains of equal length. */
+typedef struct {
+    int32_t n_chains; /* >= 1                          */
+    int32_t n_beads;  /* 2 .. SS_MAX_BEADS             */
+} ss_element;
+
+/* Parameters of the model (Sec. 2), the scheme (Sec. 3.1) and the observables.
+ * Any field left 0 takes the default in brackets. */
+typedef struct {
+    double N0;      /* beads per slip-spring, <Z>_eq = N/N0 (Eq. average_slip_spring_number_and_
+                       entanglement_bead_number); +inf switches slip-springs off [4]       */
+    double Ns;      /* slip-spring strength (Eq. free_energy_single_chain) [0.5]          */
+    double zeta_s;  /* slip-spring friction (Eqs. transition_probability_*) [0.1]         */
+    double dt;      /* time step (Sec. 3.1) [0.01]                                       */
+    double b;       /* bead size [1]                                                     */
+    double kT;      /* thermal energy [1]                                                */
+    double zeta;    /* bead friction [1]                                                 */
+    double k_b;     /* bond stiffness; 0 -> 3 kT / b^2                                   */
+    double k_s;     /* slip-spring stiffness; 0 -> 3 kT / (Ns b^2)                        */
+    int32_t create_mode;    /* 0: K = z_max - Z creation attempts per end (GPU form of
+                               Sec. 3.2); 1: K = 1 (CPU form) [0]                        */
+    int32_t z_max;          /* slip-spring slots per chain, 1..N [N]                     */
+    int32_t destroy_new;    /* 1: a spring created in a step may be destroyed in the same
+                               step; 0: only springs that existed before [0]             */
+    int32_t recenter_every; /* shift each chain and its anchors to the chain's centre of
+                               mass every this many steps when the flow is non-zero; the
+                               shift does not change any bond, spring length, rate or
+                               stress [100]; < 0 never                                  */
+    int32_t log_every;      /* ensemble stress sums every this many steps; 0: none        */
+    int32_t max_logs;       /* capacity of the stress log per element [0]                */
+    int32_t corr_levels;    /* multiple-tau levels, 1..SS_MAX_LEVELS [24]; < 0: none      */
+    int32_t groups;         /* chain groups per element for standard errors [32]         */
+    int32_t chunk_steps;    /* steps per kernel launch [1024]; 1 gives the plain
+                               one-step-per-launch form                                  */
+} ss_params;
+
+/* Create a context for n_elems elements.  precision: SS_FP32 or SS_FP64.
+ * seed keys the counter-based random numbers (Philox4x32-10): chains with the
+ * same seed and global chain id draw the same numbers in any run.  The global
+ * chain id of chain m of element e is the sum of n_chains of elements < e plus
+ * m.  cuda_stream: a cudaStream_t, or NULL for the default stream.
+ * Errors: SS_EINVAL (bad element table), SS_ENOMEM, SS_ECUDA. */
+int ss_create(ss_ctx** out, const ss_element* elems, int n_elems, int precision, uint64_t seed,
+              void* cuda_stream);
+
+/* Validate and apply parameters; allocates the device state.  Must precede the
+ * first ss_run.  Validation: every physical parameter finite and > 0 (N0 may
+ * be +inf), Euler stability dt (4 k_b + k_s)/zeta < 2, 1 <= z_max <= N.
+ * Calling it again resets the state, the observables and the step counter. */
+int ss_set_params(ss_ctx* ctx, const ss_params* p);
+
+/* Velocity gradient kappa (row-major, dR_a/dt contains kappa[3a+b] R_b) from
+ * step from_step on, for element elem (-1: all).  Later entries of the
+ * piecewise-constant schedule are replaced.  Applies to the bead update
+ * (Eq. langevin_equation_bead_position) and the anchor advection (Eq.
+ * dynamic_equation_anchoring_position). */
+int ss_set_flow(ss_ctx* ctx, int elem, int64_t from_step, const double kappa[9]);
+
+/* Enqueue n_steps time steps for every element.  The first call on fresh state
+ * samples the equilibrium initial state (Sec. 3.1: Gaussian chain, Poisson Z,
+ * uniform S, Gaussian anchors).  Returns SS_EOVERFLOW if the step counter
+ * would pass 2^32 (a Philox counter word); a non-finite state is reported by
+ * ss_status(). */
+int ss_run(ss_ctx* ctx, int64_t n_steps);
+
+/* Ensemble stress log of element elem: for each log n, t[n] is the time
+ * (steps * dt), mean[n][6] the chain average of sigma xx,yy,zz,xy,xz,yz and
+ * sem[n][6] its standard error over the chain groups (either may be NULL).
+ * Writes at most cap entries; *n_out receives the number available. */
+int ss_stress(ss_ctx* ctx, int elem, double* t, double* mean, double* sem, int cap, int* n_out);
+
+/* Relaxation modulus of element elem from the multiple-tau correlator, channel
+ * SS_CH_*: t[n] the lag (steps * dt), G[n] in rho0 kT averaged over the xy, xz,
+ * yz components, sem[n] its standard error over chain groups.  Lags are
+ * ascending; lags without samples are left out.  *n_out = number available. */
+int ss_correlator(ss_ctx* ctx, int elem, int channel, double* t, double* G, double* sem, int cap,
+                  int* n_out);
+
+/* Free every resource of the context (NULL is accepted). */
+int ss_destroy(ss_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none); static text for NULL. */
+const char* ss_last_error(const ss_ctx* ctx);
+
+/* ---- support calls -------------------------------------------------------- */
+
+/* Copy element elem's state to host arrays (any may be NULL): R[M][N][3],
+ * Z[M], S[M][z_max] (-1 for empty slots), A[M][z_max][3] (0 for empty),
+ * in FP64 whatever the precision.  Synchronises. */
+int ss_get_state(ss_ctx* ctx, int elem, double* R, int32_t* Z, int32_t* S, double* A);
+
+/* Replace element elem's state from host arrays laid out as in ss_get_state.
+ * Validation: 0 <= Z <= z_max, 0 <= S < N for j < Z, finite values.  Marks the
+ * context initialised (no equilibrium sampling on the next ss_run). */
+int ss_set_state(ss_ctx* ctx, int elem, const double* R, const int32_t* Z, const int32_t* S,
+                 const double* A);
+
+/* Steps taken so far. */
+int ss_step_count(ss_ctx* ctx, int64_t* steps);
+
+/* Zero the correlator and the stress logs (e.g. after equilibration). */
+int ss_reset_observables(ss_ctx* ctx);
+
+/* Raw correlator sums of element elem: acc[g][level][16][2][3] (lag slot,
+ * channel 0 = later sigma x origin sigma, 1 = later sigma x origin
+ * sigma + sigma_v, component xy/xz/yz) summed over the chains of group g,
+ * n_groups groups; *n_samples = samples per chain since the last reset.
+ * Level l >= 1 only fills lag slots 8..15 (lag slot k means k 2^l steps). */
+int ss_corr_sums(ss_ctx* ctx, int elem, double* acc, int* n_groups, int64_t* n_samples);
+
+/* Raw stress-log sums of element elem: sums[n][g][14] = sums over group g of
+ * sigma xx,yy,zz,xy,xz,yz, their squares, Z and Z^2; log_step[n] = steps done
+ * when log n was taken.  *n_out = logs available, *n_groups = groups. */
+int ss_log_sums(ss_ctx* ctx, int elem, int64_t* log_step, double* sums, int cap, int* n_out,
+                int* n_groups);
+
+/* Event counters summed over all chains since ss_set_params: out[0] hops to
+ * S+1, out[1] hops to S-1, out[2] springs created, out[3] springs destroyed,
+ * out[4] creation attempts dropped at capacity (K = 1 form), out[5] kernel
+ * launches, out[6] non-finite-state detections. */
+int ss_counters(ss_ctx* ctx, int64_t out[7]);
+
+/* Device status word: 0 if every step so far kept a finite state; bit 0 set
+ * if a non-finite bead position was found.  Synchronises. */
+int ss_status(ss_ctx* ctx, int32_t* status);
+
+/* Wait for the context's stream. */
+int ss_synchronize(ss_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,89 @@
+"""ctypes declarations of the C ABI in include/slipspring.h.
+
+Loading fails loudly when the compiled library is missing: there is no CPU
+fallback.  Build it with `python -m paper_1106_2899_gb300.build`.
+"""
+import ctypes as C
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libslipspring.so")
+
+SS_OK = 0
+ERRORS = {-1: "SS_EINVAL", -2: "SS_ENOMEM", -3: "SS_ECUDA", -4: "SS_EOVERFLOW", -5: "SS_ESTATE",
+          -6: "SS_ETIMEOUT"}
+SS_FP32, SS_FP64 = 0, 1
+SS_CH_AUTO, SS_CH_CROSS, SS_CH_TOTAL = 0, 1, 2
+
+# every symbol include/slipspring.h declares
+EXPORTS = ["ss_create", "ss_set_params", "ss_set_flow", "ss_run", "ss_stress", "ss_correlator",
+           "ss_destroy", "ss_last_error", "ss_get_state", "ss_set_state", "ss_step_count",
+           "ss_reset_observables", "ss_corr_sums", "ss_log_sums", "ss_counters", "ss_status",
+           "ss_synchronize"]
+
+
+class ss_element(C.Structure):
+    _fields_ = [("n_chains", C.c_int32), ("n_beads", C.c_int32)]
+
+
+class ss_params(C.Structure):
+    _fields_ = [("N0", C.c_double), ("Ns", C.c_double), ("zeta_s", C.c_double), ("dt", C.c_double),
+                ("b", C.c_double), ("kT", C.c_double), ("zeta", C.c_double), ("k_b", C.c_double),
+                ("k_s", C.c_double), ("create_mode", C.c_int32), ("z_max", C.c_int32),
+                ("destroy_new", C.c_int32), ("recenter_every", C.c_int32), ("log_every", C.c_int32),
+                ("max_logs", C.c_int32), ("corr_levels", C.c_int32), ("groups", C.c_int32),
+                ("chunk_steps", C.c_int32)]
+
+
+class SlipSpringError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library and declare its signatures (once)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise SlipSpringError(
+            "libslipspring.so not found at %s: build it with `python -m paper_1106_2899_gb300.build` "
+            "(there is no CPU fallback)" % path)
+    lib = C.CDLL(path)
+    P = C.POINTER
+    vp, dp, i32p, i64p = C.c_void_p, P(C.c_double), P(C.c_int32), P(C.c_int64)
+    sig = {
+        "ss_create": [P(vp), P(ss_element), C.c_int, C.c_int, C.c_uint64, vp],
+        "ss_set_params": [vp, P(ss_params)],
+        "ss_set_flow": [vp, C.c_int, C.c_int64, dp],
+        "ss_run": [vp, C.c_int64],
+        "ss_stress": [vp, C.c_int, dp, dp, dp, C.c_int, P(C.c_int)],
+        "ss_correlator": [vp, C.c_int, C.c_int, dp, dp, dp, C.c_int, P(C.c_int)],
+        "ss_destroy": [vp],
+        "ss_get_state": [vp, C.c_int, dp, i32p, i32p, dp],
+        "ss_set_state": [vp, C.c_int, dp, i32p, i32p, dp],
+        "ss_step_count": [vp, i64p],
+        "ss_reset_observables": [vp],
+        "ss_corr_sums": [vp, C.c_int, dp, P(C.c_int), i64p],
+        "ss_log_sums": [vp, C.c_int, i64p, dp, C.c_int, P(C.c_int), P(C.c_int)],
+        "ss_counters": [vp, i64p],
+        "ss_status": [vp, i32p],
+        "ss_synchronize": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.ss_last_error.argtypes = [vp]
+    lib.ss_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(rc: int, ctx=None, what: str = ""):
+    if rc != SS_OK:
+        msg = ""
+        if ctx is not None and _lib is not None:
+            msg = (_lib.ss_last_error(ctx) or b"").decode()
+        raise SlipSpringError("%s failed: %s %s" % (what, ERRORS.get(rc, rc), msg))

@@ -1,0 +1,166 @@
+"""Python binding of the slip-spring library: argument marshalling only.
+
+Every step of the model runs in the library's CUDA kernels; this module turns
+NumPy arrays and keyword arguments into the C ABI's pointers and structs.
+
+    ens = SlipSpring([(65536, 32)], precision="fp32", seed=1)
+    ens.set_params(N0=4, Ns=0.5, zeta_s=0.1, dt=0.01)
+    ens.run(10000)
+    t, G, sem = ens.correlator(channel="total")
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _native as nat
+
+CHANNELS = {"auto": nat.SS_CH_AUTO, "cross": nat.SS_CH_CROSS, "total": nat.SS_CH_TOTAL}
+
+
+def _p(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+class SlipSpring:
+    """A context of one or more elements (ensembles of equal-length chains)."""
+
+    def __init__(self, elements, precision="fp32", seed=0, stream=None):
+        self.lib = nat.load()
+        els = [(int(m), int(n)) for m, n in elements]
+        arr = (nat.ss_element * len(els))(*[nat.ss_element(m, n) for m, n in els])
+        self.elements = els
+        self.precision = precision
+        h = C.c_void_p()
+        prec = {"fp32": nat.SS_FP32, "fp64": nat.SS_FP64}[precision]
+        st = C.c_void_p(int(stream)) if stream is not None else None
+        nat.check(self.lib.ss_create(C.byref(h), arr, len(els), prec, int(seed), st), None, "ss_create")
+        self.h = h
+        self.params = None
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.ss_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc, what):
+        nat.check(rc, self.h, what)
+
+    # ------------------------------------------------------------ setup ---
+    def set_params(self, **kw):
+        p = nat.ss_params()
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError("unknown parameter %r" % k)
+            setattr(p, k, v)
+        self._chk(self.lib.ss_set_params(self.h, C.byref(p)), "ss_set_params")
+        self.params = dict(kw)
+
+    def set_flow(self, kappa, from_step=0, elem=-1):
+        k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(9))
+        self._chk(self.lib.ss_set_flow(self.h, int(elem), int(from_step), _p(k, C.c_double)), "ss_set_flow")
+
+    def run(self, n_steps):
+        self._chk(self.lib.ss_run(self.h, int(n_steps)), "ss_run")
+
+    def synchronize(self):
+        self._chk(self.lib.ss_synchronize(self.h), "ss_synchronize")
+
+    def reset_observables(self):
+        self._chk(self.lib.ss_reset_observables(self.h), "ss_reset_observables")
+
+    @property
+    def step(self):
+        s = C.c_int64()
+        self._chk(self.lib.ss_step_count(self.h, C.byref(s)), "ss_step_count")
+        return s.value
+
+    # ------------------------------------------------------------ state ---
+    def _zm(self, elem):
+        zm = (self.params or {}).get("z_max", 0)
+        return zm if zm > 0 else self.elements[elem][1]
+
+    def get_state(self, elem=0):
+        M, N = self.elements[elem]
+        zm = self._zm(elem)
+        R = np.zeros((M, N, 3))
+        Z = np.zeros(M, dtype=np.int32)
+        S = np.zeros((M, zm), dtype=np.int32)
+        A = np.zeros((M, zm, 3))
+        self._chk(self.lib.ss_get_state(self.h, elem, _p(R, C.c_double), _p(Z, C.c_int32), _p(S, C.c_int32),
+                                        _p(A, C.c_double)), "ss_get_state")
+        return {"R": R, "Z": Z, "S": S, "A": A}
+
+    def set_state(self, st, elem=0):
+        R = np.ascontiguousarray(st["R"], dtype=np.float64)
+        Z = np.ascontiguousarray(st["Z"], dtype=np.int32)
+        S = np.ascontiguousarray(st["S"], dtype=np.int32)
+        A = np.ascontiguousarray(st["A"], dtype=np.float64)
+        self._chk(self.lib.ss_set_state(self.h, elem, _p(R, C.c_double), _p(Z, C.c_int32), _p(S, C.c_int32),
+                                        _p(A, C.c_double)), "ss_set_state")
+
+    # ------------------------------------------------------ observables ---
+    def stress(self, elem=0):
+        """(t, mean[n][6], sem[n][6]) of sigma xx,yy,zz,xy,xz,yz at the log times."""
+        n = C.c_int()
+        self._chk(self.lib.ss_stress(self.h, elem, None, None, None, 0, C.byref(n)), "ss_stress")
+        k = n.value
+        t = np.zeros(k)
+        mean = np.zeros((k, 6))
+        sem = np.zeros((k, 6))
+        if k:
+            self._chk(self.lib.ss_stress(self.h, elem, _p(t, C.c_double), _p(mean, C.c_double),
+                                         _p(sem, C.c_double), k, C.byref(n)), "ss_stress")
+        return t, mean, sem
+
+    def correlator(self, channel="total", elem=0):
+        """(t, G, sem) of the relaxation modulus in rho0 kT (Green-Kubo, App. B)."""
+        ch = CHANNELS[channel] if isinstance(channel, str) else int(channel)
+        n = C.c_int()
+        self._chk(self.lib.ss_correlator(self.h, elem, ch, None, None, None, 0, C.byref(n)), "ss_correlator")
+        k = n.value
+        t, G, sem = np.zeros(k), np.zeros(k), np.zeros(k)
+        if k:
+            self._chk(self.lib.ss_correlator(self.h, elem, ch, _p(t, C.c_double), _p(G, C.c_double),
+                                             _p(sem, C.c_double), k, C.byref(n)), "ss_correlator")
+        return t, G, sem
+
+    def corr_sums(self, elem=0):
+        """(acc [G][levels][16][2][3], n_samples) raw correlator group sums."""
+        levels = (self.params or {}).get("corr_levels", 0) or 24
+        g = C.c_int()
+        n = C.c_int64()
+        self._chk(self.lib.ss_corr_sums(self.h, elem, None, C.byref(g), C.byref(n)), "ss_corr_sums")
+        acc = np.zeros((g.value, levels, 16, 2, 3))
+        self._chk(self.lib.ss_corr_sums(self.h, elem, _p(acc, C.c_double), C.byref(g), C.byref(n)),
+                  "ss_corr_sums")
+        return acc, n.value
+
+    def log_sums(self, elem=0):
+        """(log_step [n], sums [n][G][14]) raw stress-log group sums."""
+        n = C.c_int()
+        g = C.c_int()
+        self._chk(self.lib.ss_log_sums(self.h, elem, None, None, 0, C.byref(n), C.byref(g)), "ss_log_sums")
+        k = n.value
+        t = np.zeros(k, dtype=np.int64)
+        L = np.zeros((k, g.value, 14))
+        if k:
+            self._chk(self.lib.ss_log_sums(self.h, elem, _p(t, C.c_int64), _p(L, C.c_double), k, C.byref(n),
+                                           C.byref(g)), "ss_log_sums")
+        return t, L
+
+    def counters(self):
+        out = np.zeros(7, dtype=np.int64)
+        self._chk(self.lib.ss_counters(self.h, _p(out, C.c_int64)), "ss_counters")
+        return dict(zip(["hops_up", "hops_down", "created", "destroyed", "dropped", "launches",
+                         "nonfinite"], out.tolist()))
+
+    def status(self):
+        s = C.c_int32()
+        self._chk(self.lib.ss_status(self.h, C.byref(s)), "ss_status")
+        return s.value

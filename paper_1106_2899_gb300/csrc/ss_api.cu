@@ -1,0 +1,725 @@
+// ss_api.cu -- host runtime behind the C ABI of include/slipspring.h.
+//
+// A context holds one or more elements (ensembles of equal-length chains).
+// Each element owns its device state and observables; ss_run enqueues, per
+// chunk of chunk_steps steps, one launch of the chain kernel per element.
+// Parameters are validated here, on the host; kernels assume valid input.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "slipspring.h"
+#include "ss_kernels.cuh"
+
+namespace {
+
+constexpr int kWarpsPerCta = 8;
+constexpr int kThreads = kWarpsPerCta * 32;
+constexpr int kCorrSmemBudget = 48 * 1024;  // bytes of shared memory for correlator levels
+constexpr int kMaxSmemLevels = 7;
+
+struct Elem {
+    int M = 0, N = 0, W = 32, zmax = 0;
+    uint32_t chain_base = 0;
+    int slices = 0, groups = 0;
+    void* R = nullptr;
+    void* A = nullptr;
+    int32_t* S = nullptr;
+    int32_t* Z = nullptr;
+    void* hist = nullptr;
+    void* histg = nullptr;
+    void* accg = nullptr;
+    double* acc64 = nullptr;
+    double* logs = nullptr;
+    double* kap_d = nullptr;
+    long long* kfrom_d = nullptr;
+    int n_kap_d = 0;
+    std::vector<long long> kfrom{0};
+    std::vector<double> kap = std::vector<double>(9, 0.0);
+    bool flow_dirty = true;
+};
+
+}  // namespace
+
+struct ss_ctx {
+    cudaStream_t stream = nullptr;
+    int prec = SS_FP32;
+    uint64_t seed = 0;
+    std::vector<Elem> el;
+    ss_params P{};
+    bool have_params = false;
+    bool initialized = false;
+    double k_b = 0, k_s = 0;
+    int levels = 0, Lsm = 0;
+    long long step = 0;
+    long long nsamp = 0;
+    long long log_m0 = 0;
+    unsigned long long* counters = nullptr;  // [8]
+    int32_t* status = nullptr;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(ss_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define SS_CUDA(ctx, call)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? SS_ENOMEM : SS_ECUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+size_t tsize(const ss_ctx* c) { return c->prec == SS_FP64 ? sizeof(double) : sizeof(float); }
+
+void free_elem(Elem& e) {
+    void* ptrs[] = {e.R, e.A, e.S, e.Z, e.hist, e.histg, e.accg, e.acc64, e.logs, e.kap_d, e.kfrom_d};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    e.R = e.A = e.hist = e.histg = e.accg = nullptr;
+    e.S = e.Z = nullptr;
+    e.acc64 = e.logs = e.kap_d = nullptr;
+    e.kfrom_d = nullptr;
+    e.n_kap_d = 0;
+}
+
+int lanes_for(int N) { return N <= 16 ? 16 : 32; }
+
+int chains_per_cta(int W) { return kWarpsPerCta * (32 / W); }
+
+int smem_levels(const ss_ctx* c, int W) {
+    if (c->levels <= 1) return 0;
+    const int per_level = chains_per_cta(W) * 2 * 3 * ssk::kCells * (int)tsize(c);
+    return std::min({c->levels - 1, kMaxSmemLevels, kCorrSmemBudget / per_level});
+}
+
+// Inverse standard normal CDF by bisection on erfc: the destruction
+// threshold on a standard normal draw (host constant).
+double norm_ppf(double p) {
+    if (p >= 1.0) return std::numeric_limits<double>::infinity();
+    if (p <= 0.0) return -std::numeric_limits<double>::infinity();
+    double lo = -40.0, hi = 40.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (0.5 * std::erfc(-mid / std::sqrt(2.0)) < p)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+template <typename T>
+ssk::StepConst<T> step_const(const ss_ctx* c, int N) {
+    const ss_params& p = c->P;
+    ssk::StepConst<T> s{};
+    s.k_b = T(c->k_b);
+    s.k_s = T(c->k_s);
+    s.mob = T(p.dt / p.zeta);
+    s.amp = T(std::sqrt(2.0 * p.kT * p.dt / p.zeta));
+    s.dt = T(p.dt);
+    s.pref = T(p.dt * p.kT / p.zeta_s);
+    s.chop = T(c->k_s / (4.0 * p.kT));
+    s.sa = T(std::sqrt(p.kT / c->k_s));
+    const double pd = p.dt * p.kT / p.zeta_s;
+    s.cd = T(norm_ppf(pd < 1.0 ? pd : 1.0));
+    s.NkT = T((double)N * p.kT);
+    s.kT = T(p.kT);
+    s.pc[0] = T(0);
+    for (int K = 1; K <= ssk::kMaxBeads; ++K) {
+        double pc = p.dt * p.kT / (p.zeta_s * p.N0 * (double)K);
+        if (pc > 0.5) pc = 0.5;
+        s.pc[K] = T(pc);
+    }
+    return s;
+}
+
+template <typename T, int W>
+int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
+    const ss_params& p = c->P;
+    ssk::ChunkArgs a{};
+    a.R = e.R;
+    a.A = e.A;
+    a.S = e.S;
+    a.Z = e.Z;
+    a.hist = e.hist;
+    a.histg = e.histg;
+    a.accg = e.accg;
+    a.acc64 = e.acc64;
+    a.logs = e.logs;
+    a.counters = c->counters;
+    a.status = c->status;
+    a.kap = e.kap_d;
+    a.kap_from = e.kfrom_d;
+    a.n_kap = e.n_kap_d;
+    a.M = e.M;
+    a.N = e.N;
+    a.zmax = e.zmax;
+    a.create_mode = p.create_mode;
+    a.destroy_new = p.destroy_new;
+    a.levels = c->levels;
+    a.Lsm = c->Lsm;
+    a.log_every = p.log_every;
+    a.recenter_every = p.recenter_every;
+    a.log_m0 = c->log_m0;
+    a.max_logs = p.max_logs;
+    a.groups = e.groups;
+    a.slices = e.slices;
+    a.t0 = t0;
+    a.nsteps = nsteps;
+    a.nsamp0 = c->nsamp;
+    a.key0 = (uint32_t)c->seed;
+    a.key1 = (uint32_t)(c->seed >> 32);
+    a.chain_base = e.chain_base;
+    a.nlog_chunk = p.log_every > 0 ? (int)((t0 + nsteps) / p.log_every - t0 / p.log_every) : 0;
+    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, c->Lsm, a.nlog_chunk);
+    static int configured_bytes = 0;
+    if (plan.total > 48 * 1024 && plan.total > configured_bytes) {
+        SS_CUDA(c, cudaFuncSetAttribute(ssk::chunk_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        plan.total));
+        configured_bytes = plan.total;
+    }
+    const ssk::StepConst<T> sc = step_const<T>(c, e.N);
+    ssk::chunk_kernel<T, W><<<e.slices, kThreads, plan.total, c->stream>>>(a, sc);
+    SS_CUDA(c, cudaGetLastError());
+    c->launches++;
+    return SS_OK;
+}
+
+template <typename T>
+int dispatch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
+    if (e.W == 16) return launch_chunk<T, 16>(c, e, t0, nsteps);
+    return launch_chunk<T, 32>(c, e, t0, nsteps);
+}
+
+template <typename T>
+int launch_init(ss_ctx* c, Elem& e) {
+    const ss_params& p = c->P;
+    const double lam = (double)e.N / p.N0;
+    const double sb = std::sqrt(p.kT / c->k_b), sa = std::sqrt(p.kT / c->k_s);
+    const int blocks = (e.M + 127) / 128;
+    if (e.W == 16)
+        ssk::init_kernel<T, 16><<<blocks, 128, 0, c->stream>>>(
+            (T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb, sa, lam, (uint32_t)c->seed,
+            (uint32_t)(c->seed >> 32), e.chain_base);
+    else
+        ssk::init_kernel<T, 32><<<blocks, 128, 0, c->stream>>>(
+            (T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb, sa, lam, (uint32_t)c->seed,
+            (uint32_t)(c->seed >> 32), e.chain_base);
+    SS_CUDA(c, cudaGetLastError());
+    c->launches++;
+    return SS_OK;
+}
+
+int upload_flow(ss_ctx* c, Elem& e) {
+    if (!e.flow_dirty) return SS_OK;
+    if (e.kap_d) cudaFree(e.kap_d);
+    if (e.kfrom_d) cudaFree(e.kfrom_d);
+    e.kap_d = nullptr;
+    e.kfrom_d = nullptr;
+    const int n = (int)e.kfrom.size();
+    SS_CUDA(c, cudaMalloc(&e.kap_d, sizeof(double) * 9 * n));
+    SS_CUDA(c, cudaMalloc(&e.kfrom_d, sizeof(long long) * n));
+    SS_CUDA(c, cudaMemcpyAsync(e.kap_d, e.kap.data(), sizeof(double) * 9 * n, cudaMemcpyHostToDevice,
+                               c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(e.kfrom_d, e.kfrom.data(), sizeof(long long) * n, cudaMemcpyHostToDevice,
+                               c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    e.n_kap_d = n;
+    e.flow_dirty = false;
+    return SS_OK;
+}
+
+int zero_observables(ss_ctx* c) {
+    const size_t ts = tsize(c);
+    for (Elem& e : c->el) {
+        const int Lg = c->levels > 0 ? c->levels - 1 - c->Lsm : 0;
+        if (e.hist) SS_CUDA(c, cudaMemsetAsync(e.hist, 0, (size_t)e.M * (c->Lsm + 1) * 96 * ts, c->stream));
+        if (e.histg && Lg > 0) SS_CUDA(c, cudaMemsetAsync(e.histg, 0, (size_t)e.M * Lg * 96 * ts, c->stream));
+        if (e.accg && Lg > 0) SS_CUDA(c, cudaMemsetAsync(e.accg, 0, (size_t)e.M * Lg * 96 * ts, c->stream));
+        if (e.acc64)
+            SS_CUDA(c, cudaMemsetAsync(e.acc64, 0, (size_t)e.slices * c->levels * 96 * sizeof(double), c->stream));
+        if (e.logs && c->P.max_logs > 0)
+            SS_CUDA(c, cudaMemsetAsync(e.logs, 0, (size_t)c->P.max_logs * e.groups * 14 * sizeof(double),
+                                       c->stream));
+    }
+    c->nsamp = 0;
+    c->log_m0 = c->P.log_every > 0 ? c->step / c->P.log_every : 0;
+    return SS_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
+
+Elem* elem_at(ss_ctx* c, int e) {
+    if (!c || e < 0 || e >= (int)c->el.size()) return nullptr;
+    return &c->el[e];
+}
+
+template <typename T>
+void to_device_layout(const Elem& e, const double* R, const int32_t* Z, const int32_t* S, const double* A,
+                      std::vector<T>& Rd, std::vector<T>& Ad, std::vector<int32_t>& Sd, std::vector<int32_t>& Zd) {
+    const int W = e.W, N = e.N, zm = e.zmax;
+    Rd.assign((size_t)e.M * 3 * W, T(0));
+    Ad.assign((size_t)e.M * 3 * W, T(0));
+    Sd.assign((size_t)e.M * W, -1);
+    Zd.assign((size_t)e.M, 0);
+    for (int m = 0; m < e.M; ++m) {
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) Rd[((size_t)m * 3 + d) * W + i] = T(R[((size_t)m * N + i) * 3 + d]);
+        Zd[m] = Z[m];
+        for (int j = 0; j < Z[m]; ++j) {
+            Sd[(size_t)m * W + j] = S[(size_t)m * zm + j];
+            for (int d = 0; d < 3; ++d) Ad[((size_t)m * 3 + d) * W + j] = T(A[((size_t)m * zm + j) * 3 + d]);
+        }
+    }
+}
+
+template <typename T>
+int get_state_t(ss_ctx* c, Elem& e, double* R, int32_t* Z, int32_t* S, double* A) {
+    const int W = e.W, N = e.N, zm = e.zmax;
+    std::vector<T> Rd((size_t)e.M * 3 * W), Ad((size_t)e.M * 3 * W);
+    std::vector<int32_t> Sd((size_t)e.M * W), Zd(e.M);
+    SS_CUDA(c, cudaMemcpyAsync(Rd.data(), e.R, Rd.size() * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(Ad.data(), e.A, Ad.size() * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(Sd.data(), e.S, Sd.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(Zd.data(), e.Z, Zd.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int m = 0; m < e.M; ++m) {
+        if (R)
+            for (int i = 0; i < N; ++i)
+                for (int d = 0; d < 3; ++d) R[((size_t)m * N + i) * 3 + d] = (double)Rd[((size_t)m * 3 + d) * W + i];
+        if (Z) Z[m] = Zd[m];
+        for (int j = 0; j < zm; ++j) {
+            const bool occ = j < Zd[m];
+            if (S) S[(size_t)m * zm + j] = occ ? Sd[(size_t)m * W + j] : -1;
+            if (A)
+                for (int d = 0; d < 3; ++d)
+                    A[((size_t)m * zm + j) * 3 + d] = occ ? (double)Ad[((size_t)m * 3 + d) * W + j] : 0.0;
+        }
+    }
+    return SS_OK;
+}
+
+template <typename T>
+int set_state_t(ss_ctx* c, Elem& e, const double* R, const int32_t* Z, const int32_t* S, const double* A) {
+    std::vector<T> Rd, Ad;
+    std::vector<int32_t> Sd, Zd;
+    to_device_layout<T>(e, R, Z, S, A, Rd, Ad, Sd, Zd);
+    SS_CUDA(c, cudaMemcpyAsync(e.R, Rd.data(), Rd.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(e.A, Ad.data(), Ad.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(e.S, Sd.data(), Sd.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(e.Z, Zd.data(), Zd.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SS_OK;
+}
+
+// group sums [G][L][16][2][3] from the per-slice device sums
+int group_corr(ss_ctx* c, Elem& e, std::vector<double>& out) {
+    const int L = c->levels;
+    std::vector<double> sl((size_t)e.slices * L * 96);
+    SS_CUDA(c, cudaMemcpyAsync(sl.data(), e.acc64, sl.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    out.assign((size_t)e.groups * L * 16 * 6, 0.0);
+    for (int s = 0; s < e.slices; ++s) {
+        const int g = (int)(((long long)s * e.groups) / e.slices);
+        for (int l = 0; l < L; ++l)
+            for (int d = 0; d < 3; ++d)
+                for (int cell = 0; cell < 32; ++cell) {
+                    const int ch = cell >> 4, lag = cell & 15;
+                    out[((((size_t)g * L + l) * 16 + lag) * 2 + ch) * 3 + d] +=
+                        sl[((size_t)s * L + l) * 96 + d * 32 + cell];
+                }
+    }
+    return SS_OK;
+}
+
+int chains_in_group(const Elem& e, int g, int cpc) {
+    int n = 0;
+    for (int s = 0; s < e.slices; ++s)
+        if ((int)(((long long)s * e.groups) / e.slices) == g) n += std::min(cpc, e.M - s * cpc);
+    return n;
+}
+
+}  // namespace
+
+// ================================================================== C ABI ====
+extern "C" {
+
+int ss_create(ss_ctx** out, const ss_element* elems, int n_elems, int precision, uint64_t seed,
+              void* cuda_stream) {
+    if (!out) return SS_EINVAL;
+    *out = nullptr;
+    if (!elems || n_elems <= 0) return SS_EINVAL;
+    if (precision != SS_FP32 && precision != SS_FP64) return SS_EINVAL;
+    long long total = 0;
+    for (int i = 0; i < n_elems; ++i) {
+        if (elems[i].n_chains <= 0 || elems[i].n_beads < 2 || elems[i].n_beads > SS_MAX_BEADS) return SS_EINVAL;
+        total += elems[i].n_chains;
+    }
+    if (total > 0xFFFFFFFFll) return SS_EINVAL;
+    ss_ctx* c = new (std::nothrow) ss_ctx();
+    if (!c) return SS_ENOMEM;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->prec = precision;
+    c->seed = seed;
+    uint32_t base = 0;
+    for (int i = 0; i < n_elems; ++i) {
+        Elem e;
+        e.M = elems[i].n_chains;
+        e.N = elems[i].n_beads;
+        e.W = lanes_for(e.N);
+        e.chain_base = base;
+        base += (uint32_t)e.M;
+        c->el.push_back(e);
+    }
+    if (cudaMalloc(&c->counters, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->status, sizeof(int32_t)) != cudaSuccess) {
+        ss_destroy(c);
+        return SS_ECUDA;
+    }
+    cudaMemset(c->counters, 0, 8 * sizeof(unsigned long long));
+    cudaMemset(c->status, 0, sizeof(int32_t));
+    *out = c;
+    return SS_OK;
+}
+
+int ss_set_params(ss_ctx* c, const ss_params* pin) {
+    if (!c || !pin) return SS_EINVAL;
+    ss_params p = *pin;
+    if (p.N0 == 0) p.N0 = 4.0;
+    if (p.Ns == 0) p.Ns = 0.5;
+    if (p.zeta_s == 0) p.zeta_s = 0.1;
+    if (p.dt == 0) p.dt = 0.01;
+    if (p.b == 0) p.b = 1.0;
+    if (p.kT == 0) p.kT = 1.0;
+    if (p.zeta == 0) p.zeta = 1.0;
+    if (p.recenter_every == 0) p.recenter_every = 100;
+    if (p.corr_levels == 0) p.corr_levels = 24;
+    if (p.groups == 0) p.groups = 32;
+    if (p.chunk_steps == 0) p.chunk_steps = 1024;
+    if (!(p.N0 > 0) || std::isnan(p.N0)) return fail(c, SS_EINVAL, "N0 must be > 0 (inf allowed)");
+    if (!finite_pos(p.Ns) || !finite_pos(p.zeta_s) || !finite_pos(p.dt) || !finite_pos(p.b) ||
+        !finite_pos(p.kT) || !finite_pos(p.zeta))
+        return fail(c, SS_EINVAL, "Ns, zeta_s, dt, b, kT, zeta must be finite and > 0");
+    const double kb = p.k_b > 0 ? p.k_b : 3.0 * p.kT / (p.b * p.b);
+    const double ks = p.k_s > 0 ? p.k_s : 3.0 * p.kT / (p.Ns * p.b * p.b);
+    if (!finite_pos(kb) || !finite_pos(ks)) return fail(c, SS_EINVAL, "k_b, k_s must be finite and > 0");
+    if (!(p.dt * (4.0 * kb + ks) / p.zeta < 2.0))
+        return fail(c, SS_EINVAL, "Euler step unstable: dt (4 k_b + k_s) / zeta must be < 2");
+    if (p.create_mode != 0 && p.create_mode != 1) return fail(c, SS_EINVAL, "create_mode must be 0 or 1");
+    if (p.destroy_new != 0 && p.destroy_new != 1) return fail(c, SS_EINVAL, "destroy_new must be 0 or 1");
+    if (p.corr_levels > SS_MAX_LEVELS) return fail(c, SS_EINVAL, "corr_levels must be <= 32");
+    if (p.groups < 1 || p.chunk_steps < 1 || p.log_every < 0 || p.max_logs < 0)
+        return fail(c, SS_EINVAL, "groups, chunk_steps must be >= 1; log_every, max_logs >= 0");
+    if (p.log_every > 0 && p.max_logs <= 0) return fail(c, SS_EINVAL, "log_every > 0 needs max_logs > 0");
+    for (const Elem& e : c->el) {
+        const int zm = p.z_max > 0 ? p.z_max : e.N;
+        if (zm < 1 || zm > e.N) return fail(c, SS_EINVAL, "z_max must be in 1..N");
+    }
+    if (c->counters) cudaStreamSynchronize(c->stream);
+    for (Elem& e : c->el) free_elem(e);
+    c->P = p;
+    c->k_b = kb;
+    c->k_s = ks;
+    c->levels = p.corr_levels > 0 ? p.corr_levels : 0;
+    c->step = 0;
+    c->initialized = false;
+    int Lsm_all = kMaxSmemLevels;
+    for (const Elem& e : c->el) Lsm_all = std::min(Lsm_all, smem_levels(c, e.W));
+    c->Lsm = c->levels > 1 ? Lsm_all : 0;
+    const size_t ts = tsize(c);
+    const int Lg = c->levels > 0 ? c->levels - 1 - c->Lsm : 0;
+    for (Elem& e : c->el) {
+        e.zmax = p.z_max > 0 ? p.z_max : e.N;
+        const int cpc = chains_per_cta(e.W);
+        e.slices = (e.M + cpc - 1) / cpc;
+        e.groups = std::min(p.groups, e.slices);
+        SS_CUDA(c, cudaMalloc(&e.R, (size_t)e.M * 3 * e.W * ts));
+        SS_CUDA(c, cudaMalloc(&e.A, (size_t)e.M * 3 * e.W * ts));
+        SS_CUDA(c, cudaMalloc(&e.S, (size_t)e.M * e.W * sizeof(int32_t)));
+        SS_CUDA(c, cudaMalloc(&e.Z, (size_t)e.M * sizeof(int32_t)));
+        SS_CUDA(c, cudaMemsetAsync(e.Z, 0, (size_t)e.M * sizeof(int32_t), c->stream));
+        if (c->levels > 0) {
+            SS_CUDA(c, cudaMalloc(&e.hist, (size_t)e.M * (c->Lsm + 1) * 96 * ts));
+            if (Lg > 0) {
+                SS_CUDA(c, cudaMalloc(&e.histg, (size_t)e.M * Lg * 96 * ts));
+                SS_CUDA(c, cudaMalloc(&e.accg, (size_t)e.M * Lg * 96 * ts));
+            }
+            SS_CUDA(c, cudaMalloc(&e.acc64, (size_t)e.slices * c->levels * 96 * sizeof(double)));
+        }
+        if (p.max_logs > 0) SS_CUDA(c, cudaMalloc(&e.logs, (size_t)p.max_logs * e.groups * 14 * sizeof(double)));
+        e.flow_dirty = true;
+    }
+    SS_CUDA(c, cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned long long), c->stream));
+    SS_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int32_t), c->stream));
+    c->launches = 0;
+    int rc = zero_observables(c);
+    if (rc != SS_OK) return rc;
+    c->have_params = true;
+    return SS_OK;
+}
+
+int ss_set_flow(ss_ctx* c, int elem, int64_t from_step, const double kappa[9]) {
+    if (!c || !kappa || from_step < 0) return SS_EINVAL;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(kappa[i])) return fail(c, SS_EINVAL, "kappa must be finite");
+    if (elem < -1 || elem >= (int)c->el.size()) return fail(c, SS_EINVAL, "bad element index");
+    for (int i = 0; i < (int)c->el.size(); ++i) {
+        if (elem >= 0 && i != elem) continue;
+        Elem& e = c->el[i];
+        size_t n = 0;
+        while (n < e.kfrom.size() && e.kfrom[n] < from_step) ++n;
+        e.kfrom.resize(n + 1);
+        e.kap.resize(9 * (n + 1));
+        e.kfrom[n] = from_step;
+        for (int k = 0; k < 9; ++k) e.kap[9 * n + k] = kappa[k];
+        e.flow_dirty = true;
+    }
+    return SS_OK;
+}
+
+int ss_run(ss_ctx* c, int64_t n_steps) {
+    if (!c) return SS_EINVAL;
+    if (!c->have_params) return fail(c, SS_ESTATE, "ss_set_params must precede ss_run");
+    if (n_steps < 0) return fail(c, SS_EINVAL, "n_steps must be >= 0");
+    if (c->step + n_steps > 0xFFFFFFFFll) return fail(c, SS_EOVERFLOW, "step counter would pass 2^32");
+    const ss_params& p = c->P;
+    if (p.log_every > 0) {
+        const long long nlog = (c->step + n_steps) / p.log_every - c->log_m0;
+        if (nlog > p.max_logs) return fail(c, SS_EINVAL, "stress log capacity (max_logs) exceeded");
+    }
+    for (Elem& e : c->el) {
+        int rc = upload_flow(c, e);
+        if (rc != SS_OK) return rc;
+    }
+    if (!c->initialized) {
+        for (Elem& e : c->el) {
+            int rc = c->prec == SS_FP64 ? launch_init<double>(c, e) : launch_init<float>(c, e);
+            if (rc != SS_OK) return rc;
+        }
+        c->initialized = true;
+    }
+    long long left = n_steps;
+    while (left > 0) {
+        const int ns = (int)std::min<long long>(left, p.chunk_steps);
+        for (Elem& e : c->el) {
+            int rc = c->prec == SS_FP64 ? dispatch_chunk<double>(c, e, c->step, ns)
+                                        : dispatch_chunk<float>(c, e, c->step, ns);
+            if (rc != SS_OK) return rc;
+        }
+        c->step += ns;
+        if (c->levels > 0) c->nsamp += ns;
+        left -= ns;
+    }
+    return SS_OK;
+}
+
+int ss_stress(ss_ctx* c, int elem, double* t, double* mean, double* sem, int cap, int* n_out) {
+    Elem* e = elem_at(c, elem);
+    if (!e || cap < 0) return fail(c, SS_EINVAL, "bad element or capacity");
+    if (!c->have_params) return fail(c, SS_ESTATE, "no parameters");
+    const ss_params& p = c->P;
+    const int n = p.log_every > 0 ? (int)std::min<long long>(c->step / p.log_every - c->log_m0, p.max_logs) : 0;
+    if (n_out) *n_out = n;
+    if (n == 0 || cap == 0) return SS_OK;
+    std::vector<double> L((size_t)n * e->groups * 14);
+    SS_CUDA(c, cudaMemcpyAsync(L.data(), e->logs, L.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int cpc = chains_per_cta(e->W);
+    for (int i = 0; i < std::min(n, cap); ++i) {
+        if (t) t[i] = (double)((c->log_m0 + 1 + i) * p.log_every) * p.dt;
+        for (int k = 0; k < 6; ++k) {
+            double tot = 0.0, gm = 0.0, gm2 = 0.0;
+            for (int g = 0; g < e->groups; ++g) {
+                const double sg = L[((size_t)i * e->groups + g) * 14 + k];
+                tot += sg;
+                const double mg = sg / chains_in_group(*e, g, cpc);
+                gm += mg;
+                gm2 += mg * mg;
+            }
+            if (mean) mean[i * 6 + k] = tot / e->M;
+            if (sem) {
+                const int G = e->groups;
+                const double mu = gm / G;
+                sem[i * 6 + k] = G > 1 ? std::sqrt(std::max(0.0, (gm2 - G * mu * mu) / (G - 1)) / G) : 0.0;
+            }
+        }
+    }
+    return SS_OK;
+}
+
+int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double* sem, int cap, int* n_out) {
+    Elem* e = elem_at(c, elem);
+    if (!e || cap < 0) return fail(c, SS_EINVAL, "bad element or capacity");
+    if (channel < SS_CH_AUTO || channel > SS_CH_TOTAL) return fail(c, SS_EINVAL, "bad channel");
+    if (!c->have_params || c->levels <= 0) return fail(c, SS_ESTATE, "correlator not enabled");
+    std::vector<double> acc;
+    int rc = group_corr(c, *e, acc);
+    if (rc != SS_OK) return rc;
+    const int L = c->levels, NG = e->groups, cpc = chains_per_cta(e->W);
+    const double norm = (double)e->N * c->P.kT * c->P.kT;
+    int n = 0;
+    for (int l = 0; l < L; ++l)
+        for (int k = (l == 0 ? 0 : 8); k < 16; ++k) {
+            const long long cnt = std::max(0ll, (c->nsamp >> l) - k);
+            if (cnt <= 0) continue;
+            double tot = 0.0, gm = 0.0, gm2 = 0.0;
+            for (int g = 0; g < NG; ++g) {
+                double v = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    const double* base = &acc[((((size_t)g * L + l) * 16 + k) * 2) * 3];
+                    const double auto_ = base[d], total = base[3 + d];
+                    v += channel == SS_CH_AUTO ? auto_ : (channel == SS_CH_TOTAL ? total : total - auto_);
+                }
+                v /= 3.0;
+                tot += v;
+                const double mg = v / ((double)cnt * chains_in_group(*e, g, cpc) * norm);
+                gm += mg;
+                gm2 += mg * mg;
+            }
+            if (n < cap) {
+                if (t) t[n] = (double)((long long)k << l) * c->P.dt;
+                if (G) G[n] = tot / ((double)cnt * e->M * norm);
+                if (sem) {
+                    const double mu = gm / NG;
+                    sem[n] = NG > 1 ? std::sqrt(std::max(0.0, (gm2 - NG * mu * mu) / (NG - 1)) / NG) : 0.0;
+                }
+            }
+            ++n;
+        }
+    if (n_out) *n_out = n;
+    return SS_OK;
+}
+
+int ss_destroy(ss_ctx* c) {
+    if (!c) return SS_OK;
+    if (c->stream || c->counters) cudaStreamSynchronize(c->stream);
+    for (Elem& e : c->el) free_elem(e);
+    if (c->counters) cudaFree(c->counters);
+    if (c->status) cudaFree(c->status);
+    delete c;
+    return SS_OK;
+}
+
+const char* ss_last_error(const ss_ctx* c) {
+    if (!c) return "no context";
+    return c->err.c_str();
+}
+
+int ss_get_state(ss_ctx* c, int elem, double* R, int32_t* Z, int32_t* S, double* A) {
+    Elem* e = elem_at(c, elem);
+    if (!e) return fail(c, SS_EINVAL, "bad element");
+    if (!c->have_params) return fail(c, SS_ESTATE, "no parameters");
+    return c->prec == SS_FP64 ? get_state_t<double>(c, *e, R, Z, S, A) : get_state_t<float>(c, *e, R, Z, S, A);
+}
+
+int ss_set_state(ss_ctx* c, int elem, const double* R, const int32_t* Z, const int32_t* S, const double* A) {
+    Elem* e = elem_at(c, elem);
+    if (!e || !R || !Z || !S || !A) return fail(c, SS_EINVAL, "bad element or NULL array");
+    if (!c->have_params) return fail(c, SS_ESTATE, "ss_set_params must precede ss_set_state");
+    for (int m = 0; m < e->M; ++m) {
+        if (Z[m] < 0 || Z[m] > e->zmax) return fail(c, SS_EINVAL, "Z out of range");
+        for (int j = 0; j < Z[m]; ++j) {
+            const int s = S[(size_t)m * e->zmax + j];
+            if (s < 0 || s >= e->N) return fail(c, SS_EINVAL, "S out of range");
+            for (int d = 0; d < 3; ++d)
+                if (!std::isfinite(A[((size_t)m * e->zmax + j) * 3 + d])) return fail(c, SS_EINVAL, "non-finite A");
+        }
+        for (int i = 0; i < e->N * 3; ++i)
+            if (!std::isfinite(R[(size_t)m * e->N * 3 + i])) return fail(c, SS_EINVAL, "non-finite R");
+    }
+    int rc = c->prec == SS_FP64 ? set_state_t<double>(c, *e, R, Z, S, A) : set_state_t<float>(c, *e, R, Z, S, A);
+    if (rc != SS_OK) return rc;
+    // every element must hold a state before stepping: sample the others once
+    if (!c->initialized) {
+        for (int i = 0; i < (int)c->el.size(); ++i) {
+            if (i == elem) continue;
+            rc = c->prec == SS_FP64 ? launch_init<double>(c, c->el[i]) : launch_init<float>(c, c->el[i]);
+            if (rc != SS_OK) return rc;
+        }
+        c->initialized = true;
+    }
+    return SS_OK;
+}
+
+int ss_step_count(ss_ctx* c, int64_t* steps) {
+    if (!c || !steps) return SS_EINVAL;
+    *steps = c->step;
+    return SS_OK;
+}
+
+int ss_reset_observables(ss_ctx* c) {
+    if (!c) return SS_EINVAL;
+    if (!c->have_params) return fail(c, SS_ESTATE, "no parameters");
+    return zero_observables(c);
+}
+
+int ss_corr_sums(ss_ctx* c, int elem, double* acc, int* n_groups, int64_t* n_samples) {
+    Elem* e = elem_at(c, elem);
+    if (!e) return fail(c, SS_EINVAL, "bad element");
+    if (!c->have_params || c->levels <= 0) return fail(c, SS_ESTATE, "correlator not enabled");
+    std::vector<double> g;
+    int rc = group_corr(c, *e, g);
+    if (rc != SS_OK) return rc;
+    if (acc) std::memcpy(acc, g.data(), g.size() * sizeof(double));
+    if (n_groups) *n_groups = e->groups;
+    if (n_samples) *n_samples = c->nsamp;
+    return SS_OK;
+}
+
+int ss_log_sums(ss_ctx* c, int elem, int64_t* log_step, double* sums, int cap, int* n_out, int* n_groups) {
+    Elem* e = elem_at(c, elem);
+    if (!e || cap < 0) return fail(c, SS_EINVAL, "bad element or capacity");
+    if (!c->have_params) return fail(c, SS_ESTATE, "no parameters");
+    const ss_params& p = c->P;
+    const int n = p.log_every > 0 ? (int)std::min<long long>(c->step / p.log_every - c->log_m0, p.max_logs) : 0;
+    if (n_out) *n_out = n;
+    if (n_groups) *n_groups = e->groups;
+    const int k = std::min(n, cap);
+    if (k > 0 && sums) {
+        SS_CUDA(c, cudaMemcpyAsync(sums, e->logs, (size_t)k * e->groups * 14 * sizeof(double),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    if (log_step)
+        for (int i = 0; i < k; ++i) log_step[i] = (c->log_m0 + 1 + i) * p.log_every;
+    return SS_OK;
+}
+
+int ss_counters(ss_ctx* c, int64_t out[7]) {
+    if (!c || !out) return SS_EINVAL;
+    unsigned long long h[8] = {0};
+    SS_CUDA(c, cudaMemcpyAsync(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 5; ++i) out[i] = (int64_t)h[i];
+    out[5] = c->launches;
+    out[6] = (int64_t)h[6];
+    return SS_OK;
+}
+
+int ss_status(ss_ctx* c, int32_t* status) {
+    if (!c || !status) return SS_EINVAL;
+    SS_CUDA(c, cudaMemcpyAsync(status, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SS_OK;
+}
+
+int ss_synchronize(ss_ctx* c) {
+    if (!c) return SS_EINVAL;
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SS_OK;
+}
+
+}  // extern "C"

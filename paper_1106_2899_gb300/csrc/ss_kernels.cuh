@@ -1,0 +1,728 @@
+// ss_kernels.cuh -- sm_103a kernels of the single-chain slip-spring time step
+// (T. Uneyama, arXiv:1106.2899, Sec. 3.1), with stress sampling into a
+// multiple-tau correlator and ensemble stress logs.
+//
+// Layout: one chain per W-lane segment of a warp (W = 32: one chain per warp,
+// W = 16: two).  Lane l of a segment owns bead l and slip-spring slot l, so
+// N <= W and z_max <= N (the paper's one-slot-per-bead bound, Sec. 3.2).  A
+// launch advances each chain `nsteps` steps with its whole state in
+// registers; bond forces, hops and stresses exchange data with warp shuffles.
+//
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter = (index,
+// step, purpose, chain id), key = seed.  Per step, slot/bead index l draws
+// one block: two Box-Muller pairs give the bead noise (x, y, z) and a fourth
+// normal n3; the low bytes of the first three words give a 24-bit uniform u.
+// Slot l uses u for its hop (occupied) or its creation attempt (empty) and n3
+// for its destruction test n3 < Phi^{-1}(p_destroy).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ssk {
+
+constexpr int kP = 16;      // multiple-tau points per level
+constexpr int kCells = 32;  // (channel, lag) cells per level: channel*16 + lag
+constexpr uint32_t kPurposeStep = 1, kPurposeCreate = 2, kPurposeInitBond = 3,
+                   kPurposeInitZ = 4, kPurposeInitS = 5, kPurposeInitA = 6;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxBeads = 32;
+
+// ---------------------------------------------------------------- Philox ----
+// Ten rounds of the Philox4x32 bijection: words 0 and 2 are multiplied by
+// the two round multipliers (high and low halves kept), the high halves are
+// xored with words 1 and 3 and the round key, and the key advances by the
+// two Weyl increments after every round.
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        c0 = hi1 ^ c1 ^ k0;
+        c2 = hi0 ^ c3 ^ k1;
+        c1 = lo1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// ------------------------------------------------------------ math traits ---
+template <typename T>
+struct Mth;
+
+template <>
+struct Mth<float> {
+    static __device__ __forceinline__ float log(float x) { return __logf(x); }
+    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ void sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
+    static __device__ __forceinline__ float exp(float x) { return __expf(x); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ bool finite(float x) { return isfinite(x); }
+};
+
+template <>
+struct Mth<double> {
+    static __device__ __forceinline__ double log(double x) { return ::log(x); }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
+    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+};
+
+// pi / 2^23 in both precisions (a power-of-two scaling of pi)
+template <typename T>
+__device__ __forceinline__ T pi_over_2p23();
+template <>
+__device__ __forceinline__ float pi_over_2p23<float>() { return 3.14159265358979323846f / 8388608.0f; }
+template <>
+__device__ __forceinline__ double pi_over_2p23<double>() { return 3.14159265358979323846 / 8388608.0; }
+
+// Box-Muller pair from two words: radius sqrt(-2 ln v), v = (hi24(wa)+1)/2^24
+// in (0,1]; angle pi (2 hi24(wb)/2^24 - 1) in [-pi, pi).
+template <typename T>
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T& n_cos, T& n_sin) {
+    const T v = T((wa >> 8) + 1u) * T(1.0 / 16777216.0);
+    const T r = Mth<T>::sqrt(T(-2) * Mth<T>::log(v));
+    const T th = T(int(wb >> 8) - (1 << 23)) * pi_over_2p23<T>();
+    T s, c;
+    Mth<T>::sincos(th, &s, &c);
+    n_cos = r * c;
+    n_sin = r * s;
+}
+
+template <typename T>
+__device__ __forceinline__ T uniform_lo24(uint4 w) {
+    const uint32_t lo = (w.x & 0xFFu) | ((w.y & 0xFFu) << 8) | ((w.z & 0xFFu) << 16);
+    return T(lo) * T(1.0 / 16777216.0);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src, int width) {
+    return __shfl_sync(kFull, v, src, width);
+}
+
+// ------------------------------------------------------------- arguments ----
+template <typename T>
+struct StepConst {
+    T k_b, k_s;   // bond and slip-spring stiffness
+    T mob;        // dt / zeta
+    T amp;        // sqrt(2 kT dt / zeta)
+    T dt;
+    T pref;       // dt kT / zeta_s: hop and destruction prefactor
+    T chop;       // k_s / (4 kT): Glauber exponent per change of squared length
+    T sa;         // sqrt(kT / k_s): anchor spread of a new spring
+    T cd;         // Phi^{-1}(min(dt kT/zeta_s, 1)) (+inf when that is 1)
+    T NkT, kT;
+    T pc[kMaxBeads + 1];  // creation probability per end and attempt, by K
+};
+
+struct ChunkArgs {
+    void* R;            // [M][3][W] T
+    void* A;            // [M][3][W] T
+    int32_t* S;         // [M][W]
+    int32_t* Z;         // [M]
+    void* hist;         // [M][Lsm+1][3][32] T: correlator levels 0..Lsm between launches
+    void* histg;        // [M][Lg][3][32] T: levels Lsm+1 .. L-1
+    void* accg;         // [M][Lg][3][32] T: their partial sums within a launch
+    double* acc64;      // [slices][L][3][32]: correlator sums per CTA slice
+    double* logs;       // [max_logs][groups][14]
+    unsigned long long* counters;  // [8]
+    int32_t* status;
+    const double* kap;          // [n_kap][9]
+    const long long* kap_from;  // [n_kap]
+    int n_kap;
+    int M, N, zmax, create_mode, destroy_new;
+    int levels, Lsm;            // correlator levels (0: off), levels kept in shared memory
+    int log_every, recenter_every;
+    long long log_m0;           // logs are taken at steps m*log_every with m > log_m0
+    int max_logs, groups, slices;
+    long long t0;               // first step index of this launch
+    int nsteps;
+    long long nsamp0;           // correlator samples per chain before this launch
+    uint32_t key0, key1, chain_base;
+    int nlog_chunk;             // log slots reserved in shared memory
+};
+
+// shared memory carve-up (bytes), identical on host and device
+struct SmemPlan {
+    int off_scr, off_log, off_corr, off_red, total;
+};
+
+template <typename T>
+__host__ __device__ inline SmemPlan smem_plan(int warps, int W, int Lsm, int nlog_chunk) {
+    const int chains = warps * (32 / W);
+    SmemPlan p;
+    p.off_scr = 0;
+    int sz = warps * 32 * (int)(sizeof(int) + 3 * sizeof(T));
+    p.off_log = (sz + 15) & ~15;
+    sz = p.off_log + nlog_chunk * 14 * (int)sizeof(double);
+    p.off_corr = (sz + 15) & ~15;
+    sz = p.off_corr + chains * Lsm * 2 * 3 * kCells * (int)sizeof(T);
+    p.off_red = (sz + 15) & ~15;
+    sz = p.off_red + chains * 3 * kCells * (int)sizeof(T);
+    p.total = (sz + 15) & ~15;
+    return p;
+}
+
+// -------------------------------------------------------------- helpers -----
+// Sum over the W lanes of a segment; every lane of the segment gets the sum.
+template <typename T, int W>
+__device__ __forceinline__ T seg_sum(T v) {
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off, W);
+    return v;
+}
+
+// Glauber hop probability of Sec. 3.1 item 2, min{pref (1 - tanh y), 1/2},
+// y = chop (d_new - d_old), with 1 - tanh y written 2 / (1 + e^{2y}) and y
+// clamped to [-40, 40].
+template <typename T>
+__device__ __forceinline__ T hop_prob(const StepConst<T>& c, T d_new, T d_old) {
+    T y = c.chop * (d_new - d_old);
+    y = y > T(40) ? T(40) : (y < T(-40) ? T(-40) : y);
+    const T w = c.pref * Mth<T>::div(T(2), T(1) + Mth<T>::exp(T(2) * y));
+    return w < T(0.5) ? w : T(0.5);
+}
+
+// One multiple-tau level update for the lane's CPL cells.  hprev holds the
+// (already updated) cells of the level below; the new sample of this level is
+// the mean of the two newest samples below.  h/acc are this level's cells.
+template <typename T, int W, int CPL>
+__device__ __forceinline__ void corr_level_from_below(const T (&hprev)[3][CPL], T (&h)[3][CPL],
+                                                      T (&acc)[3][CPL], int ll, bool lag_ok) {
+    T v[3][CPL];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) v[c][k] = T(0.5) * (hprev[c][k] + __shfl_down_sync(kFull, hprev[c][k], 1, 16));
+    const bool lag0 = (ll & 15) == 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T x = shfl(v[c][0], 0, W);
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const T hs = __shfl_up_sync(kFull, h[c][k], 1, 16);
+            h[c][k] = lag0 ? v[c][k] : hs;
+            if (lag_ok) acc[c][k] += x * h[c][k];
+        }
+    }
+}
+
+// ---------------------------------------------------------- chunk kernel ----
+template <typename T, int W>
+__global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
+    constexpr int SEGS = 32 / W;
+    constexpr int CPL = kCells / W;  // correlator cells per lane
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int seg = lane / W;
+    const int ll = lane % W;
+    const int cpc = nwarps * SEGS;  // chains per CTA
+    const int cslot = warp * SEGS + seg;
+    const int m = blockIdx.x * cpc + cslot;
+    const bool live = m < a.M;
+    const int mm = live ? m : 0;
+    const uint32_t chain_id = a.chain_base + (uint32_t)mm;
+    const int N = a.N;
+    const bool is_bead = ll < N;
+    const unsigned segmask = (W == 32) ? kFull : (((1u << W) - 1u) << (seg * W));
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemPlan plan = smem_plan<T>(nwarps, W, a.Lsm, a.nlog_chunk);
+    int* scr_S = reinterpret_cast<int*>(smem + plan.off_scr) + warp * 32;
+    T* scr_A = reinterpret_cast<T*>(smem + plan.off_scr + nwarps * 32 * (int)sizeof(int)) + warp * 96;
+    double* slog = reinterpret_cast<double*>(smem + plan.off_log);
+    T* scorr = reinterpret_cast<T*>(smem + plan.off_corr);
+    T* sred = reinterpret_cast<T*>(smem + plan.off_red);
+
+    for (int i = threadIdx.x; i < a.nlog_chunk * 14; i += blockDim.x) slog[i] = 0.0;
+
+    // ---- load state
+    const T* Rg = static_cast<const T*>(a.R);
+    const T* Ag = static_cast<const T*>(a.A);
+    T R[3], A[3];
+    int Z = live ? a.Z[mm] : 0;
+    int S = (live && ll < Z) ? a.S[(size_t)mm * W + ll] : 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        R[d] = (live && is_bead) ? Rg[((size_t)mm * 3 + d) * W + ll] : T(0);
+        A[d] = (live && ll < Z) ? Ag[((size_t)mm * 3 + d) * W + ll] : T(0);
+    }
+
+    // ---- correlator state: level 0 in registers, 1..Lsm in shared memory
+    const bool corr_on = a.levels > 0;
+    T h0[3][CPL], acc0[3][CPL];
+    const T* Hs = static_cast<const T*>(a.hist);
+    const int Lsave = a.Lsm + 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const int cell = k * W + ll;
+            h0[d][k] = (corr_on && live) ? Hs[(((size_t)mm * Lsave + 0) * 3 + d) * kCells + cell] : T(0);
+            acc0[d][k] = T(0);
+        }
+    if (corr_on) {
+        for (int l = 1; l <= a.Lsm; ++l)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) {
+                    const int cell = k * W + ll;
+                    T* base = scorr + ((size_t)(cslot * a.Lsm + (l - 1)) * 2) * 96;
+                    base[d * kCells + cell] = live ? Hs[(((size_t)mm * Lsave + l) * 3 + d) * kCells + cell] : T(0);
+                    base[96 + d * kCells + cell] = T(0);
+                }
+    }
+    __syncthreads();
+
+    // ---- flow schedule
+    int ki = 0;
+    while (ki + 1 < a.n_kap && a.t0 >= a.kap_from[ki + 1]) ++ki;
+    T kap[9];
+    bool kap_nz = false;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        kap[i] = T(a.kap[ki * 9 + i]);
+        kap_nz |= (kap[i] != T(0));
+    }
+    long long next_from = (ki + 1 < a.n_kap) ? a.kap_from[ki + 1] : (1ll << 62);
+
+    unsigned cnt_up = 0, cnt_dn = 0, cnt_cr = 0, cnt_de = 0, cnt_drop = 0;
+    // steps t after which a log / a recentring happens: (t + 1) a multiple of the period
+    const long long never = 1ll << 62;
+    long long next_log = a.log_every > 0 ? (a.t0 / a.log_every + 1) * a.log_every - 1 : never;
+    long long next_rc = a.recenter_every > 0 ? (a.t0 / a.recenter_every + 1) * a.recenter_every - 1 : never;
+    int log_slot = 0;
+
+    for (int s = 0; s < a.nsteps; ++s) {
+        const long long t = a.t0 + s;
+        if (t >= next_from) {
+            while (ki + 1 < a.n_kap && t >= a.kap_from[ki + 1]) ++ki;
+            kap_nz = false;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                kap[i] = T(a.kap[ki * 9 + i]);
+                kap_nz |= (kap[i] != T(0));
+            }
+            next_from = (ki + 1 < a.n_kap) ? a.kap_from[ki + 1] : (1ll << 62);
+        }
+        // ---- random numbers of this step: block (ll, t, STEP, chain)
+        const uint4 w = philox4x32_10((uint32_t)ll, (uint32_t)t, kPurposeStep, chain_id, a.key0, a.key1);
+        T nrm[4];
+        box_muller<T>(w.x, w.y, nrm[0], nrm[1]);
+        box_muller<T>(w.z, w.w, nrm[2], nrm[3]);
+        const T u = uniform_lo24<T>(w);
+
+        // ---- substep 1: forces at time t, Euler-Maruyama, anchor advection
+        T F[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const T Rl = __shfl_up_sync(kFull, R[d], 1, W);
+            const T Rr = __shfl_down_sync(kFull, R[d], 1, W);
+            T f = T(0);
+            if (ll > 0) f += c.k_b * (Rl - R[d]);
+            if (ll < N - 1) f += c.k_b * (Rr - R[d]);
+            F[d] = f;
+        }
+        const int zloop = __reduce_max_sync(kFull, (unsigned)Z);
+        for (int j = 0; j < zloop; ++j) {
+            const int sj = __shfl_sync(kFull, S, j, W);
+            T aj[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) aj[d] = shfl(A[d], j, W);
+            if (j < Z && sj == ll) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) F[d] += c.k_s * (aj[d] - R[d]);
+            }
+        }
+        T Rn[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            T flow = T(0);
+            if (kap_nz) flow = kap[3 * d] * R[0] + kap[3 * d + 1] * R[1] + kap[3 * d + 2] * R[2];
+            Rn[d] = is_bead ? (R[d] + c.mob * F[d] + c.dt * flow + c.amp * nrm[d]) : T(0);
+        }
+        if (kap_nz && ll < Z) {
+            T An[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                An[d] = A[d] + c.dt * (kap[3 * d] * A[0] + kap[3 * d + 1] * A[1] + kap[3 * d + 2] * A[2]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) A[d] = An[d];
+        }
+
+        // ---- substep 2: hops on the new positions, one uniform per spring
+        {
+            const int si = (ll < Z) ? S : 0;
+            const int sm = si > 0 ? si - 1 : 0;
+            const int sp = si < N - 1 ? si + 1 : N - 1;
+            T d0 = T(0), dp = T(0), dm = T(0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const T r0 = shfl(Rn[d], si, W) - A[d];
+                const T rp = shfl(Rn[d], sp, W) - A[d];
+                const T rm = shfl(Rn[d], sm, W) - A[d];
+                d0 += r0 * r0;
+                dp += rp * rp;
+                dm += rm * rm;
+            }
+            if (ll < Z) {
+                const T pp = (si < N - 1) ? hop_prob<T>(c, dp, d0) : T(0);
+                const T pm = (si > 0) ? hop_prob<T>(c, dm, d0) : T(0);
+                if (u < pp) {
+                    S = si + 1;
+                    ++cnt_up;
+                } else if (u < pp + pm) {
+                    S = si - 1;
+                    ++cnt_dn;
+                }
+            }
+        }
+
+        // ---- substep 3a: creation, K attempts at both ends
+        const int Zc = Z;
+        int first = Zc, last = Zc;
+        if (Zc < a.zmax) last = (a.create_mode == 0) ? a.zmax : Zc + 1;
+        if (Zc >= a.zmax && a.create_mode == 1 && ll == 0 && live) ++cnt_drop;
+        const int K = last - first;
+        int end_new = -1;
+        if (ll >= first && ll < last) {
+            const T pc = c.pc[K];
+            if (u < pc)
+                end_new = 0;
+            else if (u < T(2) * pc)
+                end_new = N - 1;
+        }
+        T Anew[3] = {T(0), T(0), T(0)};
+        const unsigned cre_any = __ballot_sync(kFull, end_new >= 0);
+        if (cre_any) {
+            T e0[3], eN[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                e0[d] = shfl(Rn[d], 0, W);
+                eN[d] = shfl(Rn[d], N - 1, W);
+            }
+            if (end_new >= 0) {
+                const uint4 wc = philox4x32_10((uint32_t)ll, (uint32_t)t, kPurposeCreate, chain_id, a.key0, a.key1);
+                T n3[4];
+                box_muller<T>(wc.x, wc.y, n3[0], n3[1]);
+                box_muller<T>(wc.z, wc.w, n3[2], n3[3]);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) Anew[d] = (end_new == 0 ? e0[d] : eN[d]) + c.sa * n3[d];
+                ++cnt_cr;
+            }
+        }
+
+        // ---- substep 3b: destruction at the ends, then re-indexing
+        bool alive_old = ll < Zc;
+        if (ll < Zc && (S == 0 || S == N - 1) && nrm[3] < c.cd) {
+            alive_old = false;
+            ++cnt_de;
+        }
+        bool alive_new = end_new >= 0;
+        if (alive_new && a.destroy_new && nrm[3] < c.cd) {
+            alive_new = false;
+            ++cnt_de;
+        }
+        const unsigned changed = __ballot_sync(kFull, (ll < Zc && !alive_old) || end_new >= 0);
+        if (changed) {
+            const unsigned keep = __ballot_sync(kFull, alive_old) & segmask;
+            const unsigned n1 = __ballot_sync(kFull, alive_new && end_new == 0) & segmask;
+            const unsigned nN = __ballot_sync(kFull, alive_new && end_new == N - 1) & segmask;
+            const int nk = __popc(keep), n1c = __popc(n1);
+            int dest = -1;
+            if (alive_old)
+                dest = __popc(keep & lanemask_lt);
+            else if (alive_new && end_new == 0)
+                dest = nk + __popc(n1 & lanemask_lt);
+            else if (alive_new)
+                dest = nk + n1c + __popc(nN & lanemask_lt);
+            __syncwarp();
+            if (dest >= 0) {
+                scr_S[seg * W + dest] = alive_old ? S : end_new;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) scr_A[d * 32 + seg * W + dest] = alive_old ? A[d] : Anew[d];
+            }
+            __syncwarp();
+            const int Znew = nk + n1c + __popc(nN);
+            if (ll < Znew) {
+                S = scr_S[seg * W + ll];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) A[d] = scr_A[d * 32 + seg * W + ll];
+            }
+            __syncwarp();
+            Z = Znew;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) R[d] = Rn[d];
+
+        // ---- stress of the new state (Eq. stress_tensor_single_chain, App. B)
+        const bool do_log = (t == next_log);
+        if (do_log) next_log += a.log_every;
+        const bool do_rc = (t == next_rc) && kap_nz;
+        if (t == next_rc) next_rc += a.recenter_every;
+        if (corr_on || do_log) {
+            T q[3], dd[3];
+            const int si = (ll < Z) ? S : 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const T r1 = __shfl_down_sync(kFull, R[d], 1, W);
+                q[d] = (ll < N - 1) ? (r1 - R[d]) : T(0);
+                const T rs = shfl(R[d], si, W);
+                dd[d] = (ll < Z) ? (rs - A[d]) : T(0);
+            }
+            T sig[3], sgv[3];
+            sig[0] = seg_sum<T, W>(c.k_b * q[0] * q[1]);
+            sig[1] = seg_sum<T, W>(c.k_b * q[0] * q[2]);
+            sig[2] = seg_sum<T, W>(c.k_b * q[1] * q[2]);
+            sgv[0] = seg_sum<T, W>(c.k_s * dd[0] * dd[1]);
+            sgv[1] = seg_sum<T, W>(c.k_s * dd[0] * dd[2]);
+            sgv[2] = seg_sum<T, W>(c.k_s * dd[1] * dd[2]);
+            if (do_log) {
+                T dg[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) dg[d] = seg_sum<T, W>(c.k_b * q[d] * q[d]) - c.NkT;
+                const int slot = log_slot++;
+                if (live && ll == 0 && slot < a.nlog_chunk) {
+                    double* L = slog + slot * 14;
+                    const double v6[6] = {(double)dg[0], (double)dg[1], (double)dg[2],
+                                          (double)sig[0], (double)sig[1], (double)sig[2]};
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        atomicAdd(L + k, v6[k]);
+                        atomicAdd(L + 6 + k, v6[k] * v6[k]);
+                    }
+                    atomicAdd(L + 12, (double)Z);
+                    atomicAdd(L + 13, (double)Z * (double)Z);
+                }
+            }
+            if (corr_on) {
+                // level 0: every step
+                const long long n = a.nsamp0 + s + 1;
+                const bool lag0 = (ll & 15) == 0;
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int k = 0; k < CPL; ++k) {
+                        const int cell = k * W + ll;
+                        const T ins = (cell >> 4) ? sig[d] + sgv[d] : sig[d];
+                        const T hs = __shfl_up_sync(kFull, h0[d][k], 1, 16);
+                        h0[d][k] = lag0 ? ins : hs;
+                        acc0[d][k] += sig[d] * h0[d][k];
+                    }
+                // levels 1.. when the sample count is a multiple of 2^l
+                if ((n & 1) == 0 && a.levels > 1) {
+                    T hprev[3][CPL];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int k = 0; k < CPL; ++k) hprev[d][k] = h0[d][k];
+                    const bool lag_ok = (ll & 15) >= kP / 2;
+                    for (int l = 1; l < a.levels; ++l) {
+                        if ((n & ((1ll << l) - 1)) != 0) break;
+                        T h[3][CPL], ac[3][CPL];
+                        T* hb;
+                        T* ab;
+                        if (l <= a.Lsm) {
+                            hb = scorr + ((size_t)(cslot * a.Lsm + (l - 1)) * 2) * 96;
+                            ab = hb + 96;
+                        } else {
+                            const int Lg = a.levels - 1 - a.Lsm;
+                            hb = static_cast<T*>(a.histg) + ((size_t)mm * Lg + (l - 1 - a.Lsm)) * 96;
+                            ab = static_cast<T*>(a.accg) + ((size_t)mm * Lg + (l - 1 - a.Lsm)) * 96;
+                        }
+#pragma unroll
+                        for (int d = 0; d < 3; ++d)
+#pragma unroll
+                            for (int k = 0; k < CPL; ++k) {
+                                h[d][k] = hb[d * kCells + k * W + ll];
+                                ac[d][k] = ab[d * kCells + k * W + ll];
+                            }
+                        corr_level_from_below<T, W, CPL>(hprev, h, ac, ll, lag_ok);
+                        if (live) {
+#pragma unroll
+                            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                                for (int k = 0; k < CPL; ++k) {
+                                    hb[d * kCells + k * W + ll] = h[d][k];
+                                    ab[d * kCells + k * W + ll] = ac[d][k];
+                                }
+                        }
+#pragma unroll
+                        for (int d = 0; d < 3; ++d)
+#pragma unroll
+                            for (int k = 0; k < CPL; ++k) hprev[d][k] = h[d][k];
+                    }
+                }
+            }
+        }
+        if (do_rc) {
+            T com[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) com[d] = seg_sum<T, W>(is_bead ? R[d] : T(0)) / T(N);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (is_bead) R[d] -= com[d];
+                if (ll < Z) A[d] -= com[d];
+            }
+        }
+    }
+
+    // ---- store state
+    T* Rw = static_cast<T*>(a.R);
+    T* Aw = static_cast<T*>(a.A);
+    bool bad = false;
+    if (live) {
+        if (ll == 0) a.Z[mm] = Z;
+        a.S[(size_t)mm * W + ll] = (ll < Z) ? S : -1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (is_bead) {
+                Rw[((size_t)mm * 3 + d) * W + ll] = R[d];
+                bad |= !Mth<T>::finite(R[d]);
+            }
+            Aw[((size_t)mm * 3 + d) * W + ll] = (ll < Z) ? A[d] : T(0);
+        }
+    }
+    if (__any_sync(kFull, bad) && lane == 0) {
+        atomicOr(a.status, 1);
+        atomicAdd(a.counters + 6, 1ull);
+    }
+
+    // ---- event counters
+    {
+        unsigned v[5] = {cnt_up, cnt_dn, cnt_cr, cnt_de, cnt_drop};
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            unsigned x = v[k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(kFull, x, off);
+            if (lane == 0 && x) atomicAdd(a.counters + k, (unsigned long long)x);
+        }
+    }
+
+    // ---- correlator: save levels 0..Lsm, flush this launch's sums per slice
+    if (corr_on) {
+        T* Hw = static_cast<T*>(a.hist);
+        if (live) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int k = 0; k < CPL; ++k)
+                    Hw[(((size_t)mm * Lsave + 0) * 3 + d) * kCells + k * W + ll] = h0[d][k];
+            for (int l = 1; l <= a.Lsm; ++l) {
+                const T* base = scorr + ((size_t)(cslot * a.Lsm + (l - 1)) * 2) * 96;
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int k = 0; k < CPL; ++k)
+                        Hw[(((size_t)mm * Lsave + l) * 3 + d) * kCells + k * W + ll] = base[d * kCells + k * W + ll];
+            }
+        }
+        // deterministic per-slice reduction, level by level
+        double* out = a.acc64 + (size_t)blockIdx.x * a.levels * 96;
+        const int Lg = a.levels - 1 - a.Lsm;
+        for (int l = 0; l < a.levels; ++l) {
+            __syncthreads();
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) {
+                    const int cell = k * W + ll;
+                    T v;
+                    if (l == 0)
+                        v = acc0[d][k];
+                    else if (l <= a.Lsm)
+                        v = scorr[((size_t)(cslot * a.Lsm + (l - 1)) * 2) * 96 + 96 + d * kCells + cell];
+                    else {
+                        T* ab = static_cast<T*>(a.accg) + ((size_t)mm * Lg + (l - 1 - a.Lsm)) * 96;
+                        v = live ? ab[d * kCells + cell] : T(0);
+                        if (live) ab[d * kCells + cell] = T(0);
+                    }
+                    sred[(size_t)cslot * 96 + d * kCells + cell] = live ? v : T(0);
+                }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 96; i += blockDim.x) {
+                double sum = 0.0;
+                for (int q = 0; q < cpc; ++q) sum += (double)sred[(size_t)q * 96 + i];
+                out[(size_t)l * 96 + i] += sum;
+            }
+        }
+    }
+
+    // ---- stress logs: add this CTA's sums to its group
+    if (a.log_every > 0 && a.nlog_chunk > 0) {
+        __syncthreads();
+        const long long first_m = a.t0 / a.log_every + 1;  // first log multiple in or after t0+1
+        const int grp = (int)(((long long)blockIdx.x * a.groups) / a.slices);
+        for (int i = threadIdx.x; i < a.nlog_chunk * 14; i += blockDim.x) {
+            const int slot = i / 14, k = i % 14;
+            const long long idx = first_m + slot - a.log_m0 - 1;
+            const long long step = (first_m + slot) * a.log_every;
+            if (step <= a.t0 + a.nsteps && idx >= 0 && idx < a.max_logs && slog[i] != 0.0)
+                atomicAdd(a.logs + ((size_t)idx * a.groups + grp) * 14 + k, slog[i]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ init kernel ----
+// Equilibrium initial state (Sec. 3.1 sampling): ideal-chain bonds with
+// variance kT/k_b per component, Z ~ Poisson(N/N0) by inverse CDF on a 53-bit
+// uniform (capped at z_max), S uniform on the beads, anchors Gaussian around
+// their bead with variance kT/k_s.  One thread per chain, FP64 arithmetic.
+template <typename T, int W>
+__global__ void init_kernel(T* R, T* A, int32_t* S, int32_t* Z, int M, int N, int zmax, double sb,
+                            double sa, double lam, uint32_t key0, uint32_t key1, uint32_t chain_base) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const uint32_t cid = chain_base + (uint32_t)m;
+    double r[kMaxBeads][3];
+    r[0][0] = r[0][1] = r[0][2] = 0.0;
+    for (int i = 0; i + 1 < N; ++i) {
+        const uint4 w = philox4x32_10((uint32_t)i, 0u, kPurposeInitBond, cid, key0, key1);
+        double n[4];
+        box_muller<double>(w.x, w.y, n[0], n[1]);
+        box_muller<double>(w.z, w.w, n[2], n[3]);
+        for (int d = 0; d < 3; ++d) r[i + 1][d] = r[i][d] + sb * n[d];
+    }
+    for (int i = 0; i < W; ++i)
+        for (int d = 0; d < 3; ++d) R[((size_t)m * 3 + d) * W + i] = i < N ? T(r[i][d]) : T(0);
+    int z = zmax;
+    {
+        const uint4 w = philox4x32_10(0u, 0u, kPurposeInitZ, cid, key0, key1);
+        const double u53 = ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6)) / 9007199254740992.0;
+        double pmf = exp(-lam), cdf = pmf;
+        for (int k = 0; k < zmax; ++k) {
+            if (u53 < cdf) {
+                z = k;
+                break;
+            }
+            pmf *= lam / (double)(k + 1);
+            cdf += pmf;
+        }
+    }
+    Z[m] = z;
+    for (int j = 0; j < W; ++j) {
+        int sj = -1;
+        double an[3] = {0.0, 0.0, 0.0};
+        if (j < z) {
+            const uint4 ws = philox4x32_10((uint32_t)j, 0u, kPurposeInitS, cid, key0, key1);
+            sj = (int)(((unsigned long long)ws.x * (unsigned long long)N) >> 32);
+            const uint4 wa = philox4x32_10((uint32_t)j, 0u, kPurposeInitA, cid, key0, key1);
+            double n[4];
+            box_muller<double>(wa.x, wa.y, n[0], n[1]);
+            box_muller<double>(wa.z, wa.w, n[2], n[3]);
+            for (int d = 0; d < 3; ++d) an[d] = r[sj][d] + sa * n[d];
+        }
+        S[(size_t)m * W + j] = sj;
+        for (int d = 0; d < 3; ++d) A[((size_t)m * 3 + d) * W + j] = T(an[d]);
+    }
+}
+
+}  // namespace ssk
