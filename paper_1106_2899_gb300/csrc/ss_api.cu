@@ -98,11 +98,17 @@ int lanes_for(int N) { return N <= 16 ? 16 : 32; }
 
 int chains_per_cta(int W) { return kWarpsPerCta * (32 / W); }
 
+// correlator levels kept in shared memory (after the register levels)
 int smem_levels(const ss_ctx* c, int W) {
-    if (c->levels <= 1) return 0;
+    const int beyond = c->levels - 1 - ssk::kRegLevels;
+    if (beyond <= 0) return 0;
     const int per_level = chains_per_cta(W) * 2 * 3 * ssk::kCells * (int)tsize(c);
-    return std::min({c->levels - 1, kMaxSmemLevels, kCorrSmemBudget / per_level});
+    return std::max(0, std::min({beyond, kMaxSmemLevels, kCorrSmemBudget / per_level}));
 }
+
+// levels stored between launches (registers + shared memory) and in global memory
+int saved_levels(const ss_ctx* c) { return 1 + ssk::kRegLevels + c->Lsm; }
+int global_levels(const ss_ctx* c) { return std::max(0, c->levels - saved_levels(c)); }
 
 // Inverse standard normal CDF by bisection on erfc: the destruction
 // threshold on a standard normal draw (host constant).
@@ -245,8 +251,8 @@ int upload_flow(ss_ctx* c, Elem& e) {
 int zero_observables(ss_ctx* c) {
     const size_t ts = tsize(c);
     for (Elem& e : c->el) {
-        const int Lg = c->levels > 0 ? c->levels - 1 - c->Lsm : 0;
-        if (e.hist) SS_CUDA(c, cudaMemsetAsync(e.hist, 0, (size_t)e.M * (c->Lsm + 1) * 96 * ts, c->stream));
+        const int Lg = global_levels(c);
+        if (e.hist) SS_CUDA(c, cudaMemsetAsync(e.hist, 0, (size_t)e.M * saved_levels(c) * 96 * ts, c->stream));
         if (e.histg && Lg > 0) SS_CUDA(c, cudaMemsetAsync(e.histg, 0, (size_t)e.M * Lg * 96 * ts, c->stream));
         if (e.accg && Lg > 0) SS_CUDA(c, cudaMemsetAsync(e.accg, 0, (size_t)e.M * Lg * 96 * ts, c->stream));
         if (e.acc64)
@@ -438,9 +444,9 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
     c->initialized = false;
     int Lsm_all = kMaxSmemLevels;
     for (const Elem& e : c->el) Lsm_all = std::min(Lsm_all, smem_levels(c, e.W));
-    c->Lsm = c->levels > 1 ? Lsm_all : 0;
+    c->Lsm = Lsm_all;
     const size_t ts = tsize(c);
-    const int Lg = c->levels > 0 ? c->levels - 1 - c->Lsm : 0;
+    const int Lg = global_levels(c);
     for (Elem& e : c->el) {
         e.zmax = p.z_max > 0 ? p.z_max : e.N;
         const int cpc = chains_per_cta(e.W);
@@ -452,7 +458,7 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
         SS_CUDA(c, cudaMalloc(&e.Z, (size_t)e.M * sizeof(int32_t)));
         SS_CUDA(c, cudaMemsetAsync(e.Z, 0, (size_t)e.M * sizeof(int32_t), c->stream));
         if (c->levels > 0) {
-            SS_CUDA(c, cudaMalloc(&e.hist, (size_t)e.M * (c->Lsm + 1) * 96 * ts));
+            SS_CUDA(c, cudaMalloc(&e.hist, (size_t)e.M * saved_levels(c) * 96 * ts));
             if (Lg > 0) {
                 SS_CUDA(c, cudaMalloc(&e.histg, (size_t)e.M * Lg * 96 * ts));
                 SS_CUDA(c, cudaMalloc(&e.accg, (size_t)e.M * Lg * 96 * ts));

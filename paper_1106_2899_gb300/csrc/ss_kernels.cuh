@@ -36,12 +36,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
                                                uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        c0 = hi1 ^ c1 ^ k0;
-        c2 = hi0 ^ c3 ^ k1;
-        c1 = lo1;
-        c3 = lo0;
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -54,8 +54,9 @@ struct Mth;
 
 template <>
 struct Mth<float> {
-    static __device__ __forceinline__ float log(float x) { return __logf(x); }
-    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float neg2log(float x) { return __log2f(x) * -1.3862943611198906f; }
+    // sqrt of x >= 0 as x / sqrt(x); x = 0 gives 0
+    static __device__ __forceinline__ float sqrt(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
     static __device__ __forceinline__ void sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
     static __device__ __forceinline__ float exp(float x) { return __expf(x); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
@@ -64,7 +65,7 @@ struct Mth<float> {
 
 template <>
 struct Mth<double> {
-    static __device__ __forceinline__ double log(double x) { return ::log(x); }
+    static __device__ __forceinline__ double neg2log(double x) { return -2.0 * ::log(x); }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
     static __device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
     static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
@@ -85,7 +86,7 @@ __device__ __forceinline__ double pi_over_2p23<double>() { return 3.141592653589
 template <typename T>
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T& n_cos, T& n_sin) {
     const T v = T((wa >> 8) + 1u) * T(1.0 / 16777216.0);
-    const T r = Mth<T>::sqrt(T(-2) * Mth<T>::log(v));
+    const T r = Mth<T>::sqrt(Mth<T>::neg2log(v));
     const T th = T(int(wb >> 8) - (1 << 23)) * pi_over_2p23<T>();
     T s, c;
     Mth<T>::sincos(th, &s, &c);
@@ -124,8 +125,8 @@ struct ChunkArgs {
     void* A;            // [M][3][W] T
     int32_t* S;         // [M][W]
     int32_t* Z;         // [M]
-    void* hist;         // [M][Lsm+1][3][32] T: correlator levels 0..Lsm between launches
-    void* histg;        // [M][Lg][3][32] T: levels Lsm+1 .. L-1
+    void* hist;         // [M][1+kRegLevels+Lsm][3][32] T: levels kept between launches
+    void* histg;        // [M][Lg][3][32] T: the levels beyond those
     void* accg;         // [M][Lg][3][32] T: their partial sums within a launch
     double* acc64;      // [slices][L][3][32]: correlator sums per CTA slice
     double* logs;       // [max_logs][groups][14]
@@ -135,7 +136,7 @@ struct ChunkArgs {
     const long long* kap_from;  // [n_kap]
     int n_kap;
     int M, N, zmax, create_mode, destroy_new;
-    int levels, Lsm;            // correlator levels (0: off), levels kept in shared memory
+    int levels, Lsm;            // correlator levels (0: off); levels in shared memory
     int log_every, recenter_every;
     long long log_m0;           // logs are taken at steps m*log_every with m > log_m0
     int max_logs, groups, slices;
@@ -146,17 +147,36 @@ struct ChunkArgs {
     int nlog_chunk;             // log slots reserved in shared memory
 };
 
+// One slip-spring slot as the force loop reads it from shared memory:
+// anchor and bead index (-1: empty slot), 16 bytes in FP32.
+template <typename T>
+struct __align__(16) SlotRec {
+    T x, y, z;
+    int s;
+};
+
+// correlator levels kept in registers (levels 0..kRegLevels)
+#ifndef SS_REG_LEVELS
+#define SS_REG_LEVELS 2
+#endif
+constexpr int kRegLevels = SS_REG_LEVELS;
+
+// resident CTAs of 256 threads per SM the chunk kernel is compiled for
+#ifndef SS_CTAS_PER_SM
+#define SS_CTAS_PER_SM 3
+#endif
+
 // shared memory carve-up (bytes), identical on host and device
 struct SmemPlan {
-    int off_scr, off_log, off_corr, off_red, total;
+    int off_tab, off_log, off_corr, off_red, total;
 };
 
 template <typename T>
 __host__ __device__ inline SmemPlan smem_plan(int warps, int W, int Lsm, int nlog_chunk) {
     const int chains = warps * (32 / W);
     SmemPlan p;
-    p.off_scr = 0;
-    int sz = warps * 32 * (int)(sizeof(int) + 3 * sizeof(T));
+    p.off_tab = 0;
+    int sz = warps * 32 * (int)sizeof(SlotRec<T>);
     p.off_log = (sz + 15) & ~15;
     sz = p.off_log + nlog_chunk * 14 * (int)sizeof(double);
     p.off_corr = (sz + 15) & ~15;
@@ -176,6 +196,46 @@ __device__ __forceinline__ T seg_sum(T v) {
     return v;
 }
 
+// Sums of eight per-lane values over the W lanes of a segment by a transpose
+// reduction: the first three exchange rounds halve the number of values each
+// lane carries (a lane keeps one half and sends the other), the remaining
+// rounds are plain butterflies.  On return lane ll holds the total of value
+// (ll / (W/8)) & 7.
+template <typename T, int W>
+__device__ __forceinline__ T seg_reduce8(const T (&v)[8], int ll) {
+    constexpr int G = W / 8;
+    T w4[4];
+    {
+        const bool hi = (ll & (W / 2)) != 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T send = hi ? v[k] : v[k + 4];
+            const T keep = hi ? v[k + 4] : v[k];
+            w4[k] = keep + __shfl_xor_sync(kFull, send, W / 2, W);
+        }
+    }
+    T w2[2];
+    {
+        const bool hi = (ll & (W / 4)) != 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const T send = hi ? w4[k] : w4[k + 2];
+            const T keep = hi ? w4[k + 2] : w4[k];
+            w2[k] = keep + __shfl_xor_sync(kFull, send, W / 4, W);
+        }
+    }
+    T r;
+    {
+        const bool hi = (ll & (W / 8)) != 0;
+        const T send = hi ? w2[0] : w2[1];
+        const T keep = hi ? w2[1] : w2[0];
+        r = keep + __shfl_xor_sync(kFull, send, W / 8, W);
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off, W);
+    return r;
+}
+
 // Glauber hop probability of Sec. 3.1 item 2, min{pref (1 - tanh y), 1/2},
 // y = chop (d_new - d_old), with 1 - tanh y written 2 / (1 + e^{2y}) and y
 // clamped to [-40, 40].
@@ -187,35 +247,38 @@ __device__ __forceinline__ T hop_prob(const StepConst<T>& c, T d_new, T d_old) {
     return w < T(0.5) ? w : T(0.5);
 }
 
-// One multiple-tau level update for the lane's CPL cells.  hprev holds the
+// One multiple-tau level update of the lane's CPL cells.  hprev holds the
 // (already updated) cells of the level below; the new sample of this level is
-// the mean of the two newest samples below.  h/acc are this level's cells.
+// the mean of the two newest samples below (its lag-0 and lag-1 cells), which
+// enters at lag 0 of each channel; the lag products use the new sample of the
+// AUTO channel (sigma) as the later value.  Cells of lags below P/2 are
+// accumulated too and ignored on readout for levels >= 1.
 template <typename T, int W, int CPL>
 __device__ __forceinline__ void corr_level_from_below(const T (&hprev)[3][CPL], T (&h)[3][CPL],
-                                                      T (&acc)[3][CPL], int ll, bool lag_ok) {
-    T v[3][CPL];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) v[c][k] = T(0.5) * (hprev[c][k] + __shfl_down_sync(kFull, hprev[c][k], 1, 16));
+                                                      T (&acc)[3][CPL], int ll) {
     const bool lag0 = (ll & 15) == 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const T x = shfl(v[c][0], 0, W);
+        T v[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) v[k] = T(0.5) * (hprev[c][k] + __shfl_down_sync(kFull, hprev[c][k], 1, 16));
+        const T x = shfl(v[0], 0, W);
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             const T hs = __shfl_up_sync(kFull, h[c][k], 1, 16);
-            h[c][k] = lag0 ? v[c][k] : hs;
-            if (lag_ok) acc[c][k] += x * h[c][k];
+            h[c][k] = lag0 ? v[k] : hs;
+            acc[c][k] += x * h[c][k];
         }
     }
 }
 
 // ---------------------------------------------------------- chunk kernel ----
 template <typename T, int W>
-__global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
+__global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
     constexpr int SEGS = 32 / W;
     constexpr int CPL = kCells / W;  // correlator cells per lane
+    constexpr int LR = kRegLevels;
+    constexpr int G8 = W / 8;        // lanes per value group after seg_reduce8
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -234,8 +297,7 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
 
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemPlan plan = smem_plan<T>(nwarps, W, a.Lsm, a.nlog_chunk);
-    int* scr_S = reinterpret_cast<int*>(smem + plan.off_scr) + warp * 32;
-    T* scr_A = reinterpret_cast<T*>(smem + plan.off_scr + nwarps * 32 * (int)sizeof(int)) + warp * 96;
+    SlotRec<T>* tab = reinterpret_cast<SlotRec<T>*>(smem + plan.off_tab) + warp * 32 + seg * W;
     double* slog = reinterpret_cast<double*>(smem + plan.off_log);
     T* scorr = reinterpret_cast<T*>(smem + plan.off_corr);
     T* sred = reinterpret_cast<T*>(smem + plan.off_red);
@@ -254,34 +316,46 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
         A[d] = (live && ll < Z) ? Ag[((size_t)mm * 3 + d) * W + ll] : T(0);
     }
 
-    // ---- correlator state: level 0 in registers, 1..Lsm in shared memory
+    // ---- correlator: levels 0..LR in registers, LR+1..LR+Lsm in shared
+    // memory, the rest in global memory; the sums restart at every launch
     const bool corr_on = a.levels > 0;
-    T h0[3][CPL], acc0[3][CPL];
+    const int Lsave = 1 + LR + a.Lsm;  // levels stored in a.hist between launches
+    const int Lglob = a.levels - Lsave;
+    T hr[LR + 1][3][CPL], ar[LR + 1][3][CPL];
     const T* Hs = static_cast<const T*>(a.hist);
-    const int Lsave = a.Lsm + 1;
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+    for (int l = 0; l <= LR; ++l)
 #pragma unroll
-        for (int k = 0; k < CPL; ++k) {
-            const int cell = k * W + ll;
-            h0[d][k] = (corr_on && live) ? Hs[(((size_t)mm * Lsave + 0) * 3 + d) * kCells + cell] : T(0);
-            acc0[d][k] = T(0);
-        }
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                const int cell = k * W + ll;
+                hr[l][d][k] = (corr_on && live && l < a.levels)
+                                  ? Hs[(((size_t)mm * Lsave + l) * 3 + d) * kCells + cell] : T(0);
+                ar[l][d][k] = T(0);
+            }
     if (corr_on) {
-        for (int l = 1; l <= a.Lsm; ++l)
+        for (int l = 0; l < a.Lsm; ++l) {
+            T* base = scorr + ((size_t)(cslot * a.Lsm + l) * 2) * 96;
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
                     const int cell = k * W + ll;
-                    T* base = scorr + ((size_t)(cslot * a.Lsm + (l - 1)) * 2) * 96;
-                    base[d * kCells + cell] = live ? Hs[(((size_t)mm * Lsave + l) * 3 + d) * kCells + cell] : T(0);
+                    base[d * kCells + cell] =
+                        live ? Hs[(((size_t)mm * Lsave + LR + 1 + l) * 3 + d) * kCells + cell] : T(0);
                     base[96 + d * kCells + cell] = T(0);
                 }
+        }
     }
     __syncthreads();
 
-    // ---- flow schedule
+    // ---- flow schedule and periodic events, as step offsets in this launch
+    const int never = 0x7fffffff;
+    auto rel = [&](long long t_abs) -> int {
+        const long long r = t_abs - a.t0;
+        return r > (long long)never ? never : (int)r;
+    };
     int ki = 0;
     while (ki + 1 < a.n_kap && a.t0 >= a.kap_from[ki + 1]) ++ki;
     T kap[9];
@@ -291,33 +365,43 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
         kap[i] = T(a.kap[ki * 9 + i]);
         kap_nz |= (kap[i] != T(0));
     }
-    long long next_from = (ki + 1 < a.n_kap) ? a.kap_from[ki + 1] : (1ll << 62);
+    int next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
+    int next_log = a.log_every > 0 ? rel((a.t0 / a.log_every + 1) * a.log_every - 1) : never;
+    int next_rc = a.recenter_every > 0 ? rel((a.t0 / a.recenter_every + 1) * a.recenter_every - 1) : never;
+    int log_slot = 0;
+    const uint32_t t0lo = (uint32_t)a.t0;
+    const uint32_t n0lo = (uint32_t)a.nsamp0;
 
     unsigned cnt_up = 0, cnt_dn = 0, cnt_cr = 0, cnt_de = 0, cnt_drop = 0;
-    // steps t after which a log / a recentring happens: (t + 1) a multiple of the period
-    const long long never = 1ll << 62;
-    long long next_log = a.log_every > 0 ? (a.t0 / a.log_every + 1) * a.log_every - 1 : never;
-    long long next_rc = a.recenter_every > 0 ? (a.t0 / a.recenter_every + 1) * a.recenter_every - 1 : never;
-    int log_slot = 0;
 
     for (int s = 0; s < a.nsteps; ++s) {
-        const long long t = a.t0 + s;
-        if (t >= next_from) {
-            while (ki + 1 < a.n_kap && t >= a.kap_from[ki + 1]) ++ki;
+        const uint32_t t = t0lo + (uint32_t)s;
+        if (s >= next_from) {
+            while (ki + 1 < a.n_kap && a.t0 + s >= a.kap_from[ki + 1]) ++ki;
             kap_nz = false;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 kap[i] = T(a.kap[ki * 9 + i]);
                 kap_nz |= (kap[i] != T(0));
             }
-            next_from = (ki + 1 < a.n_kap) ? a.kap_from[ki + 1] : (1ll << 62);
+            next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
+        }
+        // ---- slot table for this step's force loop
+        {
+            SlotRec<T> rec;
+            rec.x = A[0];
+            rec.y = A[1];
+            rec.z = A[2];
+            rec.s = ll < Z ? S : -1;
+            tab[ll] = rec;
         }
         // ---- random numbers of this step: block (ll, t, STEP, chain)
-        const uint4 w = philox4x32_10((uint32_t)ll, (uint32_t)t, kPurposeStep, chain_id, a.key0, a.key1);
+        const uint4 w = philox4x32_10((uint32_t)ll, t, kPurposeStep, chain_id, a.key0, a.key1);
         T nrm[4];
         box_muller<T>(w.x, w.y, nrm[0], nrm[1]);
         box_muller<T>(w.z, w.w, nrm[2], nrm[3]);
         const T u = uniform_lo24<T>(w);
+        __syncwarp();
 
         // ---- substep 1: forces at time t, Euler-Maruyama, anchor advection
         T F[3];
@@ -330,16 +414,25 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
             if (ll < N - 1) f += c.k_b * (Rr - R[d]);
             F[d] = f;
         }
-        const int zloop = __reduce_max_sync(kFull, (unsigned)Z);
-        for (int j = 0; j < zloop; ++j) {
-            const int sj = __shfl_sync(kFull, S, j, W);
-            T aj[3];
+        {
+            // springs on this bead: k_s (sum_j A_j - n R), read in slot order
+            const int zloop = (__reduce_max_sync(kFull, (unsigned)Z) + 3) & ~3;
+            T sx = T(0), sy = T(0), sz = T(0), cnt = T(0);
+            for (int j = 0; j < zloop; j += 4) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) aj[d] = shfl(A[d], j, W);
-            if (j < Z && sj == ll) {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) F[d] += c.k_s * (aj[d] - R[d]);
+                for (int q = 0; q < 4; ++q) {
+                    const SlotRec<T> r = tab[j + q];
+                    if (r.s == ll) {
+                        sx += r.x;
+                        sy += r.y;
+                        sz += r.z;
+                        cnt += T(1);
+                    }
+                }
             }
+            F[0] += c.k_s * (sx - cnt * R[0]);
+            F[1] += c.k_s * (sy - cnt * R[1]);
+            F[2] += c.k_s * (sz - cnt * R[2]);
         }
         T Rn[3];
 #pragma unroll
@@ -409,7 +502,7 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
                 eN[d] = shfl(Rn[d], N - 1, W);
             }
             if (end_new >= 0) {
-                const uint4 wc = philox4x32_10((uint32_t)ll, (uint32_t)t, kPurposeCreate, chain_id, a.key0, a.key1);
+                const uint4 wc = philox4x32_10((uint32_t)ll, t, kPurposeCreate, chain_id, a.key0, a.key1);
                 T n3[4];
                 box_muller<T>(wc.x, wc.y, n3[0], n3[1]);
                 box_muller<T>(wc.z, wc.w, n3[2], n3[3]);
@@ -445,16 +538,21 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
                 dest = nk + n1c + __popc(nN & lanemask_lt);
             __syncwarp();
             if (dest >= 0) {
-                scr_S[seg * W + dest] = alive_old ? S : end_new;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) scr_A[d * 32 + seg * W + dest] = alive_old ? A[d] : Anew[d];
+                SlotRec<T> rec;
+                rec.x = alive_old ? A[0] : Anew[0];
+                rec.y = alive_old ? A[1] : Anew[1];
+                rec.z = alive_old ? A[2] : Anew[2];
+                rec.s = alive_old ? S : end_new;
+                tab[dest] = rec;
             }
             __syncwarp();
             const int Znew = nk + n1c + __popc(nN);
             if (ll < Znew) {
-                S = scr_S[seg * W + ll];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) A[d] = scr_A[d * 32 + seg * W + ll];
+                const SlotRec<T> rec = tab[ll];
+                S = rec.s;
+                A[0] = rec.x;
+                A[1] = rec.y;
+                A[2] = rec.z;
             }
             __syncwarp();
             Z = Znew;
@@ -463,10 +561,10 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
         for (int d = 0; d < 3; ++d) R[d] = Rn[d];
 
         // ---- stress of the new state (Eq. stress_tensor_single_chain, App. B)
-        const bool do_log = (t == next_log);
+        const bool do_log = (s == next_log);
         if (do_log) next_log += a.log_every;
-        const bool do_rc = (t == next_rc) && kap_nz;
-        if (t == next_rc) next_rc += a.recenter_every;
+        const bool do_rc = (s == next_rc) && kap_nz;
+        if (s == next_rc) next_rc += a.recenter_every;
         if (corr_on || do_log) {
             T q[3], dd[3];
             const int si = (ll < Z) ? S : 0;
@@ -477,13 +575,23 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
                 const T rs = shfl(R[d], si, W);
                 dd[d] = (ll < Z) ? (rs - A[d]) : T(0);
             }
-            T sig[3], sgv[3];
-            sig[0] = seg_sum<T, W>(c.k_b * q[0] * q[1]);
-            sig[1] = seg_sum<T, W>(c.k_b * q[0] * q[2]);
-            sig[2] = seg_sum<T, W>(c.k_b * q[1] * q[2]);
-            sgv[0] = seg_sum<T, W>(c.k_s * dd[0] * dd[1]);
-            sgv[1] = seg_sum<T, W>(c.k_s * dd[0] * dd[2]);
-            sgv[2] = seg_sum<T, W>(c.k_s * dd[1] * dd[2]);
+            // per-lane parts of sigma_ab (bonds) and sigma_ab + sigma^(v)_ab
+            T v[8];
+            v[0] = c.k_b * q[0] * q[1];
+            v[1] = c.k_b * q[0] * q[2];
+            v[2] = c.k_b * q[1] * q[2];
+            v[3] = v[0] + c.k_s * dd[0] * dd[1];
+            v[4] = v[1] + c.k_s * dd[0] * dd[2];
+            v[5] = v[2] + c.k_s * dd[1] * dd[2];
+            v[6] = T(0);
+            v[7] = T(0);
+            const T red = seg_reduce8<T, W>(v, ll);
+            T sig[3], tot[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                sig[d] = shfl(red, d * G8, W);
+                tot[d] = shfl(red, (3 + d) * G8, W);
+            }
             if (do_log) {
                 T dg[3];
 #pragma unroll
@@ -503,39 +611,43 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
                 }
             }
             if (corr_on) {
-                // level 0: every step
-                const long long n = a.nsamp0 + s + 1;
+                const uint32_t n = n0lo + (uint32_t)s + 1u;  // samples after this one
                 const bool lag0 = (ll & 15) == 0;
+                // level 0: every step
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
 #pragma unroll
                     for (int k = 0; k < CPL; ++k) {
                         const int cell = k * W + ll;
-                        const T ins = (cell >> 4) ? sig[d] + sgv[d] : sig[d];
-                        const T hs = __shfl_up_sync(kFull, h0[d][k], 1, 16);
-                        h0[d][k] = lag0 ? ins : hs;
-                        acc0[d][k] += sig[d] * h0[d][k];
+                        const T ins = (cell >> 4) ? tot[d] : sig[d];
+                        const T hs = __shfl_up_sync(kFull, hr[0][d][k], 1, 16);
+                        hr[0][d][k] = lag0 ? ins : hs;
+                        ar[0][d][k] += sig[d] * hr[0][d][k];
                     }
-                // levels 1.. when the sample count is a multiple of 2^l
-                if ((n & 1) == 0 && a.levels > 1) {
+                // register levels: level l when n is a multiple of 2^l
+#pragma unroll
+                for (int l = 1; l <= LR; ++l) {
+                    if (l < a.levels && (n & ((1u << l) - 1u)) == 0u)
+                        corr_level_from_below<T, W, CPL>(hr[l - 1], hr[l], ar[l], ll);
+                }
+                // shared and global levels
+                if (LR + 1 < a.levels && (n & ((1u << (LR + 1)) - 1u)) == 0u) {
                     T hprev[3][CPL];
 #pragma unroll
                     for (int d = 0; d < 3; ++d)
 #pragma unroll
-                        for (int k = 0; k < CPL; ++k) hprev[d][k] = h0[d][k];
-                    const bool lag_ok = (ll & 15) >= kP / 2;
-                    for (int l = 1; l < a.levels; ++l) {
-                        if ((n & ((1ll << l) - 1)) != 0) break;
+                        for (int k = 0; k < CPL; ++k) hprev[d][k] = hr[LR][d][k];
+                    for (int l = LR + 1; l < a.levels; ++l) {
+                        if (l < 32 && (n & ((1u << l) - 1u)) != 0u) break;
                         T h[3][CPL], ac[3][CPL];
                         T* hb;
                         T* ab;
-                        if (l <= a.Lsm) {
-                            hb = scorr + ((size_t)(cslot * a.Lsm + (l - 1)) * 2) * 96;
+                        if (l < Lsave) {
+                            hb = scorr + ((size_t)(cslot * a.Lsm + (l - LR - 1)) * 2) * 96;
                             ab = hb + 96;
                         } else {
-                            const int Lg = a.levels - 1 - a.Lsm;
-                            hb = static_cast<T*>(a.histg) + ((size_t)mm * Lg + (l - 1 - a.Lsm)) * 96;
-                            ab = static_cast<T*>(a.accg) + ((size_t)mm * Lg + (l - 1 - a.Lsm)) * 96;
+                            hb = static_cast<T*>(a.histg) + ((size_t)mm * Lglob + (l - Lsave)) * 96;
+                            ab = static_cast<T*>(a.accg) + ((size_t)mm * Lglob + (l - Lsave)) * 96;
                         }
 #pragma unroll
                         for (int d = 0; d < 3; ++d)
@@ -544,8 +656,8 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
                                 h[d][k] = hb[d * kCells + k * W + ll];
                                 ac[d][k] = ab[d * kCells + k * W + ll];
                             }
-                        corr_level_from_below<T, W, CPL>(hprev, h, ac, ll, lag_ok);
-                        if (live) {
+                        corr_level_from_below<T, W, CPL>(hprev, h, ac, ll);
+                        if (live || l < Lsave) {
 #pragma unroll
                             for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -607,27 +719,31 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
         }
     }
 
-    // ---- correlator: save levels 0..Lsm, flush this launch's sums per slice
+    // ---- correlator: save the stored levels, flush this launch's sums per slice
     if (corr_on) {
         T* Hw = static_cast<T*>(a.hist);
         if (live) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-                for (int k = 0; k < CPL; ++k)
-                    Hw[(((size_t)mm * Lsave + 0) * 3 + d) * kCells + k * W + ll] = h0[d][k];
-            for (int l = 1; l <= a.Lsm; ++l) {
-                const T* base = scorr + ((size_t)(cslot * a.Lsm + (l - 1)) * 2) * 96;
+            for (int l = 0; l <= LR; ++l) {
+                if (l >= a.levels) break;
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
 #pragma unroll
                     for (int k = 0; k < CPL; ++k)
-                        Hw[(((size_t)mm * Lsave + l) * 3 + d) * kCells + k * W + ll] = base[d * kCells + k * W + ll];
+                        Hw[(((size_t)mm * Lsave + l) * 3 + d) * kCells + k * W + ll] = hr[l][d][k];
+            }
+            for (int l = 0; l < a.Lsm; ++l) {
+                const T* base = scorr + ((size_t)(cslot * a.Lsm + l) * 2) * 96;
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int k = 0; k < CPL; ++k)
+                        Hw[(((size_t)mm * Lsave + LR + 1 + l) * 3 + d) * kCells + k * W + ll] =
+                            base[d * kCells + k * W + ll];
             }
         }
         // deterministic per-slice reduction, level by level
         double* out = a.acc64 + (size_t)blockIdx.x * a.levels * 96;
-        const int Lg = a.levels - 1 - a.Lsm;
         for (int l = 0; l < a.levels; ++l) {
             __syncthreads();
 #pragma unroll
@@ -635,13 +751,15 @@ __global__ void __launch_bounds__(256) chunk_kernel(const ChunkArgs a, const Ste
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
                     const int cell = k * W + ll;
-                    T v;
-                    if (l == 0)
-                        v = acc0[d][k];
-                    else if (l <= a.Lsm)
-                        v = scorr[((size_t)(cslot * a.Lsm + (l - 1)) * 2) * 96 + 96 + d * kCells + cell];
-                    else {
-                        T* ab = static_cast<T*>(a.accg) + ((size_t)mm * Lg + (l - 1 - a.Lsm)) * 96;
+                    T v = T(0);
+                    if (l <= LR) {
+#pragma unroll
+                        for (int r = 0; r <= LR; ++r)
+                            if (r == l) v = ar[r][d][k];
+                    } else if (l < Lsave) {
+                        v = scorr[((size_t)(cslot * a.Lsm + (l - LR - 1)) * 2) * 96 + 96 + d * kCells + cell];
+                    } else {
+                        T* ab = static_cast<T*>(a.accg) + ((size_t)mm * Lglob + (l - Lsave)) * 96;
                         v = live ? ab[d * kCells + cell] : T(0);
                         if (live) ab[d * kCells + cell] = T(0);
                     }
