@@ -46,6 +46,7 @@ extern "C" {
 #define SS_EOVERFLOW (-4)  /* non-finite state, or the step counter would wrap 2^32 */
 #define SS_ESTATE (-5)     /* call out of order (e.g. ss_run before ss_set_params)  */
 #define SS_ETIMEOUT (-6)   /* reserved: a bounded device wait gave up              */
+#define SS_ETOOBIG (-7)    /* request needs more than the no-allocation scratch    */
 
 /* precisions */
 #define SS_FP32 0 /* FP32 beads and anchors, FP64 ensemble sums */
@@ -190,6 +191,48 @@ int ss_status(ss_ctx* ctx, int32_t* status);
 
 /* Wait for the context's stream. */
 int ss_synchronize(ss_ctx* ctx);
+
+/* ---- allocation-free run ---------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * call cudaMalloc: code that runs while a CUDA graph is being captured, code
+ * inside a host that owns all device memory through its own pool, and
+ * real-time loops where an allocation could block.  It advances caller-owned
+ * device state by n_steps with the same chain kernel as ss_run, and keeps the
+ * kernel's working memory (correlator history, per-block partial sums, event
+ * counters, the flow) in one file-scope device array of SS_NOALLOC_SCRATCH_BYTES
+ * bytes that every GPU which loads the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * State (device pointers, read and written in place), with W = 16 lanes per
+ * chain when n_beads <= 16 and W = 32 otherwise:
+ *   R [n_chains][3][W], A [n_chains][3][W] (float for SS_FP32, double for
+ *   SS_FP64; entries beyond n_beads / beyond Z are ignored), S [n_chains][W]
+ *   int32 bead index of slot j (j < Z), Z [n_chains] int32.
+ * params: as ss_set_params (log_every must be 0; chunk_steps splits the call
+ *   into launches); z_max <= n_beads.  kappa: row-major constant velocity
+ *   gradient for the whole call (host array), NULL for none.
+ * seed, chain_base, t0: Philox key, global id of chain 0 and the index of the
+ *   first step, so that consecutive calls with t0 advanced by n_steps draw the
+ *   same numbers as one ss_run of the same chains.
+ * corr_out (device, may be NULL): [corr_levels][16][2][3] double sums over all
+ *   chains of the correlator products of this call alone (laid out as in
+ *   ss_corr_sums for one group); the correlator history starts empty at every
+ *   call.  status_out (device, may be NULL): set to 0, or 1 if a non-finite
+ *   bead position was produced.
+ * Errors: SS_EINVAL for invalid arguments, SS_ETOOBIG when the request needs
+ *   more scratch than SS_NOALLOC_SCRATCH_BYTES (it grows with n_chains and
+ *   corr_levels), SS_EOVERFLOW if t0 + n_steps passes 2^32, SS_ECUDA.
+ * The first call on a device looks up the device address of the array (with
+ *   that device current) and caches it; make that first call before any stream
+ *   capture.  Every call, on any stream, uses the same array and leaves its
+ *   contents behind; each call clears what must start at zero.  Calls that
+ *   overlap on the GPU race on the array: serialise them (one stream, or
+ *   events). */
+#define SS_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ss_run_noalloc(const ss_params* params, int precision, uint64_t seed, int32_t n_chains,
+                   int32_t n_beads, uint32_t chain_base, int64_t t0, int64_t n_steps,
+                   const double* kappa, void* R, void* A, int32_t* S, int32_t* Z, double* corr_out,
+                   int32_t* status_out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -10,7 +10,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libslipspri
 
 SS_OK = 0
 ERRORS = {-1: "SS_EINVAL", -2: "SS_ENOMEM", -3: "SS_ECUDA", -4: "SS_EOVERFLOW", -5: "SS_ESTATE",
-          -6: "SS_ETIMEOUT"}
+          -6: "SS_ETIMEOUT", -7: "SS_ETOOBIG"}
+SS_NOALLOC_SCRATCH_BYTES = 32 << 20
 SS_FP32, SS_FP64 = 0, 1
 SS_CH_AUTO, SS_CH_CROSS, SS_CH_TOTAL = 0, 1, 2
 
@@ -18,7 +19,7 @@ SS_CH_AUTO, SS_CH_CROSS, SS_CH_TOTAL = 0, 1, 2
 EXPORTS = ["ss_create", "ss_set_params", "ss_set_flow", "ss_run", "ss_stress", "ss_correlator",
            "ss_destroy", "ss_last_error", "ss_get_state", "ss_set_state", "ss_step_count",
            "ss_reset_observables", "ss_corr_sums", "ss_log_sums", "ss_counters", "ss_status",
-           "ss_synchronize"]
+           "ss_synchronize", "ss_run_noalloc"]
 
 
 class ss_element(C.Structure):
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH):
         "ss_counters": [vp, i64p],
         "ss_status": [vp, i32p],
         "ss_synchronize": [vp],
+        "ss_run_noalloc": [P(ss_params), C.c_int, C.c_uint64, C.c_int32, C.c_int32, C.c_uint32, C.c_int64,
+                           C.c_int64, dp, vp, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

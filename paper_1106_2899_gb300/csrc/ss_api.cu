@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -729,3 +730,220 @@ int ss_synchronize(ss_ctx* c) {
 }
 
 }  // extern "C"
+
+// ====================================================== allocation-free run ===
+// Working memory of ss_run_noalloc: one array per GPU for the life of the
+// process.  In host code g_noalloc_scratch names a host-side stand-in, not a
+// device address; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once).
+int noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SS_ECUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SS_ECUDA;
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return SS_OK;
+}
+
+// Slice sums [slices][L][3][32] -> one output [L][16][2][3], slices added in order.
+__global__ void noalloc_reduce_kernel(const double* acc64, int slices, int L, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L * 96) return;
+    const int l = i / 96, r = i % 96, d = r / 32, cell = r % 32;
+    double sum = 0.0;
+    for (int sl = 0; sl < slices; ++sl) sum += acc64[((size_t)sl * L + l) * 96 + r];
+    out[((l * 16 + (cell & 15)) * 2 + (cell >> 4)) * 3 + d] = sum;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T, int W>
+int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint32_t chain_base, int64_t t0,
+                     int64_t n_steps, void* R, void* A, int32_t* S, int32_t* Z, unsigned char* scr,
+                     size_t off_hist, size_t off_histg, size_t off_accg, size_t off_acc64, size_t off_kap,
+                     size_t off_kfrom, size_t off_cnt, size_t off_status, cudaStream_t st) {
+    ssk::ChunkArgs a{};
+    a.R = R;
+    a.A = A;
+    a.S = S;
+    a.Z = Z;
+    a.hist = scr + off_hist;
+    a.histg = scr + off_histg;
+    a.accg = scr + off_accg;
+    a.acc64 = reinterpret_cast<double*>(scr + off_acc64);
+    a.logs = nullptr;
+    a.counters = reinterpret_cast<unsigned long long*>(scr + off_cnt);
+    a.status = reinterpret_cast<int32_t*>(scr + off_status);
+    a.kap = reinterpret_cast<const double*>(scr + off_kap);
+    a.kap_from = reinterpret_cast<const long long*>(scr + off_kfrom);
+    a.n_kap = 1;
+    a.M = M;
+    a.N = N;
+    a.zmax = zmax;
+    a.create_mode = p.create_mode;
+    a.destroy_new = p.destroy_new;
+    a.levels = c->levels;
+    a.Lsm = c->Lsm;
+    a.log_every = 0;
+    a.recenter_every = p.recenter_every;
+    a.log_m0 = 0;
+    a.max_logs = 0;
+    a.groups = 1;
+    a.slices = (M + chains_per_cta(W) - 1) / chains_per_cta(W);
+    a.key0 = (uint32_t)c->seed;
+    a.key1 = (uint32_t)(c->seed >> 32);
+    a.chain_base = chain_base;
+    a.nlog_chunk = 0;
+    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, c->Lsm, 0);
+    if (plan.total > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(ssk::chunk_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             plan.total);
+        if (e != cudaSuccess) return SS_ECUDA;
+    }
+    const ssk::StepConst<T> sc = step_const<T>(c, N);
+    int64_t done = 0;
+    while (done < n_steps) {
+        const int ns = (int)std::min<int64_t>(n_steps - done, p.chunk_steps);
+        a.t0 = t0 + done;
+        a.nsteps = ns;
+        a.nsamp0 = done;
+        ssk::chunk_kernel<T, W><<<a.slices, kThreads, plan.total, st>>>(a, sc);
+        if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
+        done += ns;
+    }
+    return SS_OK;
+}
+
+}  // namespace
+
+extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t seed, int32_t n_chains,
+                              int32_t n_beads, uint32_t chain_base, int64_t t0, int64_t n_steps,
+                              const double* kappa, void* R, void* A, int32_t* S, int32_t* Z, double* corr_out,
+                              int32_t* status_out, void* cuda_stream) {
+    if (!params || !R || !A || !S || !Z) return SS_EINVAL;
+    if (precision != SS_FP32 && precision != SS_FP64) return SS_EINVAL;
+    if (n_chains <= 0 || n_beads < 2 || n_beads > SS_MAX_BEADS || t0 < 0 || n_steps < 0) return SS_EINVAL;
+    if ((long long)chain_base + n_chains > 0xFFFFFFFFll) return SS_EINVAL;
+    if (t0 + n_steps > 0xFFFFFFFFll) return SS_EOVERFLOW;
+    if (params->log_every != 0) return SS_EINVAL;
+    if (kappa)
+        for (int i = 0; i < 9; ++i)
+            if (!std::isfinite(kappa[i])) return SS_EINVAL;
+    // Parameter validation and defaults through a context that owns no device
+    // memory (ss_set_params with no elements allocates nothing).
+    ss_ctx c;
+    c.prec = precision;
+    c.seed = seed;
+    Elem e;
+    e.M = n_chains;
+    e.N = n_beads;
+    e.W = lanes_for(n_beads);
+    c.el.push_back(e);
+    {
+        ss_params q = *params;
+        // the validation of ss_set_params without its allocations
+        if (q.N0 == 0) q.N0 = 4.0;
+        if (q.Ns == 0) q.Ns = 0.5;
+        if (q.zeta_s == 0) q.zeta_s = 0.1;
+        if (q.dt == 0) q.dt = 0.01;
+        if (q.b == 0) q.b = 1.0;
+        if (q.kT == 0) q.kT = 1.0;
+        if (q.zeta == 0) q.zeta = 1.0;
+        if (q.recenter_every == 0) q.recenter_every = 100;
+        if (q.corr_levels == 0) q.corr_levels = 24;
+        if (q.chunk_steps == 0) q.chunk_steps = 1024;
+        if (!(q.N0 > 0) || std::isnan(q.N0)) return SS_EINVAL;
+        if (!finite_pos(q.Ns) || !finite_pos(q.zeta_s) || !finite_pos(q.dt) || !finite_pos(q.b) ||
+            !finite_pos(q.kT) || !finite_pos(q.zeta))
+            return SS_EINVAL;
+        const double kb = q.k_b > 0 ? q.k_b : 3.0 * q.kT / (q.b * q.b);
+        const double ks = q.k_s > 0 ? q.k_s : 3.0 * q.kT / (q.Ns * q.b * q.b);
+        if (!finite_pos(kb) || !finite_pos(ks) || !(q.dt * (4.0 * kb + ks) / q.zeta < 2.0)) return SS_EINVAL;
+        if ((q.create_mode != 0 && q.create_mode != 1) || (q.destroy_new != 0 && q.destroy_new != 1))
+            return SS_EINVAL;
+        if (q.corr_levels > SS_MAX_LEVELS || q.chunk_steps < 1) return SS_EINVAL;
+        const int zm = q.z_max > 0 ? q.z_max : n_beads;
+        if (zm < 1 || zm > n_beads) return SS_EINVAL;
+        c.P = q;
+        c.k_b = kb;
+        c.k_s = ks;
+        c.levels = q.corr_levels > 0 ? q.corr_levels : 0;
+        c.Lsm = smem_levels(&c, e.W);
+        c.el[0].zmax = zm;
+    }
+    // scratch layout
+    const size_t ts = tsize(&c);
+    const int W = e.W;
+    const int slices = (n_chains + chains_per_cta(W) - 1) / chains_per_cta(W);
+    const int Lsave = saved_levels(&c), Lg = global_levels(&c);
+    const bool corr = c.levels > 0;
+    size_t off = 0;
+    const size_t off_hist = off;
+    off = align256(off + (corr ? (size_t)n_chains * Lsave * 96 * ts : 0));
+    const size_t off_histg = off;
+    off = align256(off + (corr ? (size_t)n_chains * Lg * 96 * ts : 0));
+    const size_t off_accg = off;
+    off = align256(off + (corr ? (size_t)n_chains * Lg * 96 * ts : 0));
+    const size_t off_acc64 = off;
+    off = align256(off + (corr ? (size_t)slices * c.levels * 96 * sizeof(double) : 0));
+    const size_t off_kap = off;
+    off = align256(off + 9 * sizeof(double));
+    const size_t off_kfrom = off;
+    off = align256(off + sizeof(long long));
+    const size_t off_cnt = off;
+    off = align256(off + 8 * sizeof(unsigned long long));
+    const size_t off_status = off;
+    off = align256(off + sizeof(int32_t));
+    if (off > (size_t)SS_NOALLOC_SCRATCH_BYTES) return SS_ETOOBIG;
+
+    unsigned char* scr = nullptr;
+    int rc = noalloc_scratch(&scr);
+    if (rc != SS_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // what must start at zero: history, partial sums, counters, status
+    if (cudaMemsetAsync(scr, 0, off, st) != cudaSuccess) return SS_ECUDA;
+    double kap_h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (kappa) std::memcpy(kap_h, kappa, sizeof(kap_h));
+    // a copy from pageable host memory is staged before cudaMemcpyAsync returns,
+    // so kap_h may go out of scope afterwards
+    if (cudaMemcpyAsync(scr + off_kap, kap_h, sizeof(kap_h), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SS_ECUDA;
+    const int zm = c.el[0].zmax;
+    if (precision == SS_FP64)
+        rc = W == 16 ? noalloc_launches<double, 16>(&c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A,
+                                                    S, Z, scr, off_hist, off_histg, off_accg, off_acc64, off_kap,
+                                                    off_kfrom, off_cnt, off_status, st)
+                     : noalloc_launches<double, 32>(&c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A,
+                                                    S, Z, scr, off_hist, off_histg, off_accg, off_acc64, off_kap,
+                                                    off_kfrom, off_cnt, off_status, st);
+    else
+        rc = W == 16 ? noalloc_launches<float, 16>(&c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A,
+                                                   S, Z, scr, off_hist, off_histg, off_accg, off_acc64, off_kap,
+                                                   off_kfrom, off_cnt, off_status, st)
+                     : noalloc_launches<float, 32>(&c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A,
+                                                   S, Z, scr, off_hist, off_histg, off_accg, off_acc64, off_kap,
+                                                   off_kfrom, off_cnt, off_status, st);
+    if (rc != SS_OK) return rc;
+    if (corr_out && corr) {
+        const int n = c.levels * 96;
+        noalloc_reduce_kernel<<<(n + 127) / 128, 128, 0, st>>>(reinterpret_cast<const double*>(scr + off_acc64),
+                                                                slices, c.levels, corr_out);
+        if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
+    }
+    if (status_out &&
+        cudaMemcpyAsync(status_out, scr + off_status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SS_ECUDA;
+    return SS_OK;
+}
