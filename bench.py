@@ -224,7 +224,7 @@ def run_ours(args):
     e2e_s = _max_over_ranks(time.perf_counter() - te, ws)
     e2e_value = float(M) * N * spc * e2e_steps * ws / e2e_s
     h2d = M * 3 * 32 * 4 * 2 + M * 32 * 4 + M * 4
-    slices = (M + 7) // 8
+    slices = (M + 63) // 64
     d2h = slices * w["levels"] * 96 * 8
     ge.close()
 

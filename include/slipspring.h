@@ -59,7 +59,7 @@ extern "C" {
 
 #define SS_CORR_POINTS 16 /* multiple-tau points per level */
 #define SS_MAX_LEVELS 32
-#define SS_MAX_BEADS 32   /* chain length limit of this build             */
+#define SS_MAX_BEADS 64   /* chain length limit of this build             */
 
 typedef struct ss_ctx ss_ctx;
 
@@ -203,10 +203,10 @@ int ss_synchronize(ss_ctx* ctx);
  * bytes that every GPU which loads the library holds until the process exits.
  * It calls no cudaMalloc, cudaFree or allocating library routine.
  *
- * State (device pointers, read and written in place), with W = 16 lanes per
- * chain when n_beads <= 16 and W = 32 otherwise:
- *   R [n_chains][3][W], A [n_chains][3][W] (float for SS_FP32, double for
- *   SS_FP64; entries beyond n_beads / beyond Z are ignored), S [n_chains][W]
+ * State (device pointers, read and written in place), with NP = n_beads
+ * rounded up to a multiple of 16:
+ *   R [n_chains][3][NP], A [n_chains][3][NP] (float for SS_FP32, double for
+ *   SS_FP64; entries beyond n_beads / beyond Z are ignored), S [n_chains][NP]
  *   int32 bead index of slot j (j < Z), Z [n_chains] int32.
  * params: as ss_set_params (log_every must be 0; chunk_steps splits the call
  *   into launches); z_max <= n_beads.  kappa: row-major constant velocity

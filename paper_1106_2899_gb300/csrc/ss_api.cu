@@ -20,13 +20,13 @@
 
 namespace {
 
-constexpr int kWarpsPerCta = 8;
-constexpr int kThreads = kWarpsPerCta * 32;
+constexpr int kThreads = ssk::kChunkThreads;
+constexpr int kWarpsPerCta = kThreads / 32;
 constexpr int kCorrSmemBudget = 48 * 1024;  // bytes of shared memory for correlator levels
 constexpr int kMaxSmemLevels = 7;
 
 struct Elem {
-    int M = 0, N = 0, W = 32, zmax = 0;
+    int M = 0, N = 0, W = 16, B = 2, NP = 32, zmax = 0;
     uint32_t chain_base = 0;
     int slices = 0, groups = 0;
     void* R = nullptr;
@@ -35,7 +35,7 @@ struct Elem {
     int32_t* Z = nullptr;
     void* hist = nullptr;
     void* histg = nullptr;
-    void* accg = nullptr;
+    void* accc = nullptr;
     double* acc64 = nullptr;
     double* logs = nullptr;
     double* kap_d = nullptr;
@@ -85,17 +85,34 @@ int fail(ss_ctx* c, int code, const std::string& msg) {
 size_t tsize(const ss_ctx* c) { return c->prec == SS_FP64 ? sizeof(double) : sizeof(float); }
 
 void free_elem(Elem& e) {
-    void* ptrs[] = {e.R, e.A, e.S, e.Z, e.hist, e.histg, e.accg, e.acc64, e.logs, e.kap_d, e.kfrom_d};
+    void* ptrs[] = {e.R, e.A, e.S, e.Z, e.hist, e.histg, e.accc, e.acc64, e.logs, e.kap_d, e.kfrom_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    e.R = e.A = e.hist = e.histg = e.accg = nullptr;
+    e.R = e.A = e.hist = e.histg = e.accc = nullptr;
     e.S = e.Z = nullptr;
     e.acc64 = e.logs = e.kap_d = nullptr;
     e.kfrom_d = nullptr;
     e.n_kap_d = 0;
 }
 
-int lanes_for(int N) { return N <= 16 ? 16 : 32; }
+// Chain layout for N beads: W lanes per chain, B beads per lane (NP = W*B).
+#ifndef SS_N32_LAYOUT_W32
+#define SS_N32_LAYOUT_W32 0
+#endif
+void layout_for(int N, int* W, int* B) {
+    if (N <= 16) {
+        *W = 16, *B = 1;
+    } else if (N <= 32) {
+        if (SS_N32_LAYOUT_W32)
+            *W = 32, *B = 1;
+        else
+            *W = 16, *B = 2;
+    } else if (N <= 48) {
+        *W = 16, *B = 3;
+    } else {
+        *W = 16, *B = 4;
+    }
+}
 
 int chains_per_cta(int W) { return kWarpsPerCta * (32 / W); }
 
@@ -105,6 +122,14 @@ int smem_levels(const ss_ctx* c, int W) {
     if (beyond <= 0) return 0;
     const int per_level = chains_per_cta(W) * 2 * 3 * ssk::kCells * (int)tsize(c);
     return std::max(0, std::min({beyond, kMaxSmemLevels, kCorrSmemBudget / per_level}));
+}
+
+// Correlator levels that receive a sample among samples n0+1 .. n0+ns.
+unsigned long long new_sample_levels(long long n0, long long ns, int L) {
+    unsigned long long mask = 0;
+    for (int l = 0; l < L && l < 63; ++l)
+        if (((n0 + ns) >> l) > (n0 >> l)) mask |= 1ull << l;
+    return mask;
 }
 
 // levels stored between launches (registers + shared memory) and in global memory
@@ -150,10 +175,19 @@ ssk::StepConst<T> step_const(const ss_ctx* c, int N) {
         if (pc > 0.5) pc = 0.5;
         s.pc[K] = T(pc);
     }
+    s.two_pref = T(2.0 * p.dt * p.kT / p.zeta_s);
+    s.c2 = T(2.0 * (c->k_s / (4.0 * p.kT)) * 1.4426950408889634);
+    uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        s.rk0[r] = k0;
+        s.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
     return s;
 }
 
-template <typename T, int W>
+template <typename T, int W, int B>
 int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     const ss_params& p = c->P;
     ssk::ChunkArgs a{};
@@ -163,8 +197,7 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     a.Z = e.Z;
     a.hist = e.hist;
     a.histg = e.histg;
-    a.accg = e.accg;
-    a.acc64 = e.acc64;
+    a.accc = e.accc;
     a.logs = e.logs;
     a.counters = c->counters;
     a.status = c->status;
@@ -191,24 +224,37 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     a.key1 = (uint32_t)(c->seed >> 32);
     a.chain_base = e.chain_base;
     a.nlog_chunk = p.log_every > 0 ? (int)((t0 + nsteps) / p.log_every - t0 / p.log_every) : 0;
-    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, c->Lsm, a.nlog_chunk);
+    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, c->Lsm, a.nlog_chunk);
     static int configured_bytes = 0;
     if (plan.total > 48 * 1024 && plan.total > configured_bytes) {
-        SS_CUDA(c, cudaFuncSetAttribute(ssk::chunk_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SS_CUDA(c, cudaFuncSetAttribute(ssk::chunk_kernel<T, W, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         plan.total));
         configured_bytes = plan.total;
     }
     const ssk::StepConst<T> sc = step_const<T>(c, e.N);
-    ssk::chunk_kernel<T, W><<<e.slices, kThreads, plan.total, c->stream>>>(a, sc);
+    const int ctas = (e.M + chains_per_cta(W) - 1) / chains_per_cta(W);
+    ssk::chunk_kernel<T, W, B><<<ctas, kThreads, plan.total, c->stream>>>(a, sc);
     SS_CUDA(c, cudaGetLastError());
     c->launches++;
+    if (c->levels > 0) {
+        const unsigned long long mask = new_sample_levels(c->nsamp, nsteps, c->levels);
+        ssk::corr_reduce_kernel<T><<<dim3(e.slices, c->levels), 96, 0, c->stream>>>(
+            static_cast<T*>(e.accc), e.acc64, e.M, c->levels, ssk::kSliceChains, mask);
+        SS_CUDA(c, cudaGetLastError());
+        c->launches++;
+    }
     return SS_OK;
 }
 
 template <typename T>
 int dispatch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
-    if (e.W == 16) return launch_chunk<T, 16>(c, e, t0, nsteps);
-    return launch_chunk<T, 32>(c, e, t0, nsteps);
+    if (e.W == 32) return launch_chunk<T, 32, 1>(c, e, t0, nsteps);
+    switch (e.B) {
+        case 1: return launch_chunk<T, 16, 1>(c, e, t0, nsteps);
+        case 2: return launch_chunk<T, 16, 2>(c, e, t0, nsteps);
+        case 3: return launch_chunk<T, 16, 3>(c, e, t0, nsteps);
+        default: return launch_chunk<T, 16, 4>(c, e, t0, nsteps);
+    }
 }
 
 template <typename T>
@@ -217,14 +263,24 @@ int launch_init(ss_ctx* c, Elem& e) {
     const double lam = (double)e.N / p.N0;
     const double sb = std::sqrt(p.kT / c->k_b), sa = std::sqrt(p.kT / c->k_s);
     const int blocks = (e.M + 127) / 128;
-    if (e.W == 16)
-        ssk::init_kernel<T, 16><<<blocks, 128, 0, c->stream>>>(
-            (T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb, sa, lam, (uint32_t)c->seed,
-            (uint32_t)(c->seed >> 32), e.chain_base);
-    else
-        ssk::init_kernel<T, 32><<<blocks, 128, 0, c->stream>>>(
-            (T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb, sa, lam, (uint32_t)c->seed,
-            (uint32_t)(c->seed >> 32), e.chain_base);
+    const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
+    switch (e.NP) {
+        case 16:
+            ssk::init_kernel<T, 16><<<blocks, 128, 0, c->stream>>>((T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb,
+                                                                   sa, lam, k0, k1, e.chain_base);
+            break;
+        case 32:
+            ssk::init_kernel<T, 32><<<blocks, 128, 0, c->stream>>>((T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb,
+                                                                   sa, lam, k0, k1, e.chain_base);
+            break;
+        case 48:
+            ssk::init_kernel<T, 48><<<blocks, 128, 0, c->stream>>>((T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb,
+                                                                   sa, lam, k0, k1, e.chain_base);
+            break;
+        default:
+            ssk::init_kernel<T, 64><<<blocks, 128, 0, c->stream>>>((T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb,
+                                                                   sa, lam, k0, k1, e.chain_base);
+    }
     SS_CUDA(c, cudaGetLastError());
     c->launches++;
     return SS_OK;
@@ -255,7 +311,7 @@ int zero_observables(ss_ctx* c) {
         const int Lg = global_levels(c);
         if (e.hist) SS_CUDA(c, cudaMemsetAsync(e.hist, 0, (size_t)e.M * saved_levels(c) * 96 * ts, c->stream));
         if (e.histg && Lg > 0) SS_CUDA(c, cudaMemsetAsync(e.histg, 0, (size_t)e.M * Lg * 96 * ts, c->stream));
-        if (e.accg && Lg > 0) SS_CUDA(c, cudaMemsetAsync(e.accg, 0, (size_t)e.M * Lg * 96 * ts, c->stream));
+        if (e.accc) SS_CUDA(c, cudaMemsetAsync(e.accc, 0, (size_t)e.M * c->levels * 96 * ts, c->stream));
         if (e.acc64)
             SS_CUDA(c, cudaMemsetAsync(e.acc64, 0, (size_t)e.slices * c->levels * 96 * sizeof(double), c->stream));
         if (e.logs && c->P.max_logs > 0)
@@ -277,7 +333,7 @@ Elem* elem_at(ss_ctx* c, int e) {
 template <typename T>
 void to_device_layout(const Elem& e, const double* R, const int32_t* Z, const int32_t* S, const double* A,
                       std::vector<T>& Rd, std::vector<T>& Ad, std::vector<int32_t>& Sd, std::vector<int32_t>& Zd) {
-    const int W = e.W, N = e.N, zm = e.zmax;
+    const int W = e.NP, N = e.N, zm = e.zmax;
     Rd.assign((size_t)e.M * 3 * W, T(0));
     Ad.assign((size_t)e.M * 3 * W, T(0));
     Sd.assign((size_t)e.M * W, -1);
@@ -295,7 +351,7 @@ void to_device_layout(const Elem& e, const double* R, const int32_t* Z, const in
 
 template <typename T>
 int get_state_t(ss_ctx* c, Elem& e, double* R, int32_t* Z, int32_t* S, double* A) {
-    const int W = e.W, N = e.N, zm = e.zmax;
+    const int W = e.NP, N = e.N, zm = e.zmax;
     std::vector<T> Rd((size_t)e.M * 3 * W), Ad((size_t)e.M * 3 * W);
     std::vector<int32_t> Sd((size_t)e.M * W), Zd(e.M);
     SS_CUDA(c, cudaMemcpyAsync(Rd.data(), e.R, Rd.size() * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
@@ -352,10 +408,11 @@ int group_corr(ss_ctx* c, Elem& e, std::vector<double>& out) {
     return SS_OK;
 }
 
-int chains_in_group(const Elem& e, int g, int cpc) {
+int chains_in_group(const Elem& e, int g) {
+    const int sc = ssk::kSliceChains;
     int n = 0;
     for (int s = 0; s < e.slices; ++s)
-        if ((int)(((long long)s * e.groups) / e.slices) == g) n += std::min(cpc, e.M - s * cpc);
+        if ((int)(((long long)s * e.groups) / e.slices) == g) n += std::min(sc, e.M - s * sc);
     return n;
 }
 
@@ -386,7 +443,8 @@ int ss_create(ss_ctx** out, const ss_element* elems, int n_elems, int precision,
         Elem e;
         e.M = elems[i].n_chains;
         e.N = elems[i].n_beads;
-        e.W = lanes_for(e.N);
+        layout_for(e.N, &e.W, &e.B);
+        e.NP = e.W * e.B;
         e.chain_base = base;
         base += (uint32_t)e.M;
         c->el.push_back(e);
@@ -450,20 +508,17 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
     const int Lg = global_levels(c);
     for (Elem& e : c->el) {
         e.zmax = p.z_max > 0 ? p.z_max : e.N;
-        const int cpc = chains_per_cta(e.W);
-        e.slices = (e.M + cpc - 1) / cpc;
+        e.slices = (e.M + ssk::kSliceChains - 1) / ssk::kSliceChains;
         e.groups = std::min(p.groups, e.slices);
-        SS_CUDA(c, cudaMalloc(&e.R, (size_t)e.M * 3 * e.W * ts));
-        SS_CUDA(c, cudaMalloc(&e.A, (size_t)e.M * 3 * e.W * ts));
-        SS_CUDA(c, cudaMalloc(&e.S, (size_t)e.M * e.W * sizeof(int32_t)));
+        SS_CUDA(c, cudaMalloc(&e.R, (size_t)e.M * 3 * e.NP * ts));
+        SS_CUDA(c, cudaMalloc(&e.A, (size_t)e.M * 3 * e.NP * ts));
+        SS_CUDA(c, cudaMalloc(&e.S, (size_t)e.M * e.NP * sizeof(int32_t)));
         SS_CUDA(c, cudaMalloc(&e.Z, (size_t)e.M * sizeof(int32_t)));
         SS_CUDA(c, cudaMemsetAsync(e.Z, 0, (size_t)e.M * sizeof(int32_t), c->stream));
         if (c->levels > 0) {
             SS_CUDA(c, cudaMalloc(&e.hist, (size_t)e.M * saved_levels(c) * 96 * ts));
-            if (Lg > 0) {
-                SS_CUDA(c, cudaMalloc(&e.histg, (size_t)e.M * Lg * 96 * ts));
-                SS_CUDA(c, cudaMalloc(&e.accg, (size_t)e.M * Lg * 96 * ts));
-            }
+            if (Lg > 0) SS_CUDA(c, cudaMalloc(&e.histg, (size_t)e.M * Lg * 96 * ts));
+            SS_CUDA(c, cudaMalloc(&e.accc, (size_t)e.M * c->levels * 96 * ts));
             SS_CUDA(c, cudaMalloc(&e.acc64, (size_t)e.slices * c->levels * 96 * sizeof(double)));
         }
         if (p.max_logs > 0) SS_CUDA(c, cudaMalloc(&e.logs, (size_t)p.max_logs * e.groups * 14 * sizeof(double)));
@@ -544,7 +599,6 @@ int ss_stress(ss_ctx* c, int elem, double* t, double* mean, double* sem, int cap
     std::vector<double> L((size_t)n * e->groups * 14);
     SS_CUDA(c, cudaMemcpyAsync(L.data(), e->logs, L.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SS_CUDA(c, cudaStreamSynchronize(c->stream));
-    const int cpc = chains_per_cta(e->W);
     for (int i = 0; i < std::min(n, cap); ++i) {
         if (t) t[i] = (double)((c->log_m0 + 1 + i) * p.log_every) * p.dt;
         for (int k = 0; k < 6; ++k) {
@@ -552,7 +606,7 @@ int ss_stress(ss_ctx* c, int elem, double* t, double* mean, double* sem, int cap
             for (int g = 0; g < e->groups; ++g) {
                 const double sg = L[((size_t)i * e->groups + g) * 14 + k];
                 tot += sg;
-                const double mg = sg / chains_in_group(*e, g, cpc);
+                const double mg = sg / chains_in_group(*e, g);
                 gm += mg;
                 gm2 += mg * mg;
             }
@@ -575,7 +629,7 @@ int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double
     std::vector<double> acc;
     int rc = group_corr(c, *e, acc);
     if (rc != SS_OK) return rc;
-    const int L = c->levels, NG = e->groups, cpc = chains_per_cta(e->W);
+    const int L = c->levels, NG = e->groups;
     const double norm = (double)e->N * c->P.kT * c->P.kT;
     int n = 0;
     for (int l = 0; l < L; ++l)
@@ -592,7 +646,7 @@ int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double
                 }
                 v /= 3.0;
                 tot += v;
-                const double mg = v / ((double)cnt * chains_in_group(*e, g, cpc) * norm);
+                const double mg = v / ((double)cnt * chains_in_group(*e, g) * norm);
                 gm += mg;
                 gm2 += mg * mg;
             }
@@ -769,10 +823,10 @@ __global__ void noalloc_reduce_kernel(const double* acc64, int slices, int L, do
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <typename T, int W>
+template <typename T, int W, int B>
 int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint32_t chain_base, int64_t t0,
                      int64_t n_steps, void* R, void* A, int32_t* S, int32_t* Z, unsigned char* scr,
-                     size_t off_hist, size_t off_histg, size_t off_accg, size_t off_acc64, size_t off_kap,
+                     size_t off_hist, size_t off_histg, size_t off_accc, size_t off_acc64, size_t off_kap,
                      size_t off_kfrom, size_t off_cnt, size_t off_status, cudaStream_t st) {
     ssk::ChunkArgs a{};
     a.R = R;
@@ -781,8 +835,7 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
     a.Z = Z;
     a.hist = scr + off_hist;
     a.histg = scr + off_histg;
-    a.accg = scr + off_accg;
-    a.acc64 = reinterpret_cast<double*>(scr + off_acc64);
+    a.accc = scr + off_accc;
     a.logs = nullptr;
     a.counters = reinterpret_cast<unsigned long long*>(scr + off_cnt);
     a.status = reinterpret_cast<int32_t*>(scr + off_status);
@@ -801,14 +854,14 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
     a.log_m0 = 0;
     a.max_logs = 0;
     a.groups = 1;
-    a.slices = (M + chains_per_cta(W) - 1) / chains_per_cta(W);
+    a.slices = (M + ssk::kSliceChains - 1) / ssk::kSliceChains;
     a.key0 = (uint32_t)c->seed;
     a.key1 = (uint32_t)(c->seed >> 32);
     a.chain_base = chain_base;
     a.nlog_chunk = 0;
-    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, c->Lsm, 0);
+    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, c->Lsm, 0);
     if (plan.total > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(ssk::chunk_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(ssk::chunk_kernel<T, W, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              plan.total);
         if (e != cudaSuccess) return SS_ECUDA;
     }
@@ -819,8 +872,14 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
         a.t0 = t0 + done;
         a.nsteps = ns;
         a.nsamp0 = done;
-        ssk::chunk_kernel<T, W><<<a.slices, kThreads, plan.total, st>>>(a, sc);
+        ssk::chunk_kernel<T, W, B><<<(M + chains_per_cta(W) - 1) / chains_per_cta(W), kThreads, plan.total, st>>>(a, sc);
         if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
+        if (c->levels > 0) {
+            ssk::corr_reduce_kernel<T><<<dim3(a.slices, c->levels), 96, 0, st>>>(
+                static_cast<T*>(a.accc), reinterpret_cast<double*>(scr + off_acc64), M, c->levels,
+                ssk::kSliceChains, new_sample_levels(done, ns, c->levels));
+            if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
+        }
         done += ns;
     }
     return SS_OK;
@@ -849,7 +908,8 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
     Elem e;
     e.M = n_chains;
     e.N = n_beads;
-    e.W = lanes_for(n_beads);
+    layout_for(n_beads, &e.W, &e.B);
+    e.NP = e.W * e.B;
     c.el.push_back(e);
     {
         ss_params q = *params;
@@ -886,7 +946,7 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
     // scratch layout
     const size_t ts = tsize(&c);
     const int W = e.W;
-    const int slices = (n_chains + chains_per_cta(W) - 1) / chains_per_cta(W);
+    const int slices = (n_chains + ssk::kSliceChains - 1) / ssk::kSliceChains;
     const int Lsave = saved_levels(&c), Lg = global_levels(&c);
     const bool corr = c.levels > 0;
     size_t off = 0;
@@ -894,8 +954,8 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
     off = align256(off + (corr ? (size_t)n_chains * Lsave * 96 * ts : 0));
     const size_t off_histg = off;
     off = align256(off + (corr ? (size_t)n_chains * Lg * 96 * ts : 0));
-    const size_t off_accg = off;
-    off = align256(off + (corr ? (size_t)n_chains * Lg * 96 * ts : 0));
+    const size_t off_accc = off;
+    off = align256(off + (corr ? (size_t)n_chains * c.levels * 96 * ts : 0));
     const size_t off_acc64 = off;
     off = align256(off + (corr ? (size_t)slices * c.levels * 96 * sizeof(double) : 0));
     const size_t off_kap = off;
@@ -921,20 +981,23 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
     if (cudaMemcpyAsync(scr + off_kap, kap_h, sizeof(kap_h), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return SS_ECUDA;
     const int zm = c.el[0].zmax;
-    if (precision == SS_FP64)
-        rc = W == 16 ? noalloc_launches<double, 16>(&c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A,
-                                                    S, Z, scr, off_hist, off_histg, off_accg, off_acc64, off_kap,
-                                                    off_kfrom, off_cnt, off_status, st)
-                     : noalloc_launches<double, 32>(&c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A,
-                                                    S, Z, scr, off_hist, off_histg, off_accg, off_acc64, off_kap,
-                                                    off_kfrom, off_cnt, off_status, st);
-    else
-        rc = W == 16 ? noalloc_launches<float, 16>(&c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A,
-                                                   S, Z, scr, off_hist, off_histg, off_accg, off_acc64, off_kap,
-                                                   off_kfrom, off_cnt, off_status, st)
-                     : noalloc_launches<float, 32>(&c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A,
-                                                   S, Z, scr, off_hist, off_histg, off_accg, off_acc64, off_kap,
-                                                   off_kfrom, off_cnt, off_status, st);
+#define SS_NOALLOC_ARGS                                                                                          \
+    &c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A, S, Z, scr, off_hist, off_histg, off_accc,    \
+        off_acc64, off_kap, off_kfrom, off_cnt, off_status, st
+    if (precision == SS_FP64) {
+        if (e.W == 32) rc = noalloc_launches<double, 32, 1>(SS_NOALLOC_ARGS);
+        else if (e.B == 1) rc = noalloc_launches<double, 16, 1>(SS_NOALLOC_ARGS);
+        else if (e.B == 2) rc = noalloc_launches<double, 16, 2>(SS_NOALLOC_ARGS);
+        else if (e.B == 3) rc = noalloc_launches<double, 16, 3>(SS_NOALLOC_ARGS);
+        else rc = noalloc_launches<double, 16, 4>(SS_NOALLOC_ARGS);
+    } else {
+        if (e.W == 32) rc = noalloc_launches<float, 32, 1>(SS_NOALLOC_ARGS);
+        else if (e.B == 1) rc = noalloc_launches<float, 16, 1>(SS_NOALLOC_ARGS);
+        else if (e.B == 2) rc = noalloc_launches<float, 16, 2>(SS_NOALLOC_ARGS);
+        else if (e.B == 3) rc = noalloc_launches<float, 16, 3>(SS_NOALLOC_ARGS);
+        else rc = noalloc_launches<float, 16, 4>(SS_NOALLOC_ARGS);
+    }
+#undef SS_NOALLOC_ARGS
     if (rc != SS_OK) return rc;
     if (corr_out && corr) {
         const int n = c.levels * 96;

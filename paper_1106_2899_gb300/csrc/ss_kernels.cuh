@@ -3,10 +3,11 @@
 // multiple-tau correlator and ensemble stress logs.
 //
 // Layout: one chain per W-lane segment of a warp (W = 32: one chain per warp,
-// W = 16: two).  Lane l of a segment owns bead l and slip-spring slot l, so
-// N <= W and z_max <= N (the paper's one-slot-per-bead bound, Sec. 3.2).  A
-// launch advances each chain `nsteps` steps with its whole state in
-// registers; bond forces, hops and stresses exchange data with warp shuffles.
+// W = 16: two), B beads per lane: lane l of a segment owns beads and
+// slip-spring slots l, l + W, ..., so N <= W*B and z_max <= N (the paper's
+// one-slot-per-bead bound, Sec. 3.2).  A launch advances each chain `nsteps`
+// steps with its whole state in registers; neighbouring beads are read from a
+// per-warp shared-memory position table, stresses are reduced with shuffles.
 //
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter = (index,
 // step, purpose, chain id), key = seed.  Per step, slot/bead index l draws
@@ -25,7 +26,8 @@ constexpr int kCells = 32;  // (channel, lag) cells per level: channel*16 + lag
 constexpr uint32_t kPurposeStep = 1, kPurposeCreate = 2, kPurposeInitBond = 3,
                    kPurposeInitZ = 4, kPurposeInitS = 5, kPurposeInitA = 6;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxBeads = 32;
+constexpr int kMaxBeads = 64;
+constexpr int kSliceChains = 64;  // chains per FP64 correlator/log slice
 
 // ---------------------------------------------------------------- Philox ----
 // Ten rounds of the Philox4x32 bijection: words 0 and 2 are multiplied by
@@ -44,6 +46,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
         c3 = (uint32_t)p0;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// The same bijection with the ten round keys precomputed (kernel parameters).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                  const uint32_t (&rk0)[10], const uint32_t (&rk1)[10]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r];
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
     }
     return make_uint4(c0, c1, c2, c3);
 }
@@ -118,6 +135,9 @@ struct StepConst {
     T cd;         // Phi^{-1}(min(dt kT/zeta_s, 1)) (+inf when that is 1)
     T NkT, kT;
     T pc[kMaxBeads + 1];  // creation probability per end and attempt, by K
+    T two_pref;           // 2 dt kT / zeta_s
+    T c2;                 // 2 chop log2(e): base-2 exponent per change of squared length
+    uint32_t rk0[10], rk1[10];  // Philox round keys (key + r * Weyl increment)
 };
 
 struct ChunkArgs {
@@ -127,8 +147,9 @@ struct ChunkArgs {
     int32_t* Z;         // [M]
     void* hist;         // [M][1+kRegLevels+Lsm][3][32] T: levels kept between launches
     void* histg;        // [M][Lg][3][32] T: the levels beyond those
-    void* accg;         // [M][Lg][3][32] T: their partial sums within a launch
-    double* acc64;      // [slices][L][3][32]: correlator sums per CTA slice
+    void* accc;         // [M][L][3][32] T: each chain's correlator sums of this launch
+                        // (levels kept on chip are stored at the end, the others
+                        // accumulate here); a reduce kernel folds them into acc64
     double* logs;       // [max_logs][groups][14]
     unsigned long long* counters;  // [8]
     int32_t* status;
@@ -139,7 +160,7 @@ struct ChunkArgs {
     int levels, Lsm;            // correlator levels (0: off); levels in shared memory
     int log_every, recenter_every;
     long long log_m0;           // logs are taken at steps m*log_every with m > log_m0
-    int max_logs, groups, slices;
+    int max_logs, groups, slices;  // slices of kSliceChains chains
     long long t0;               // first step index of this launch
     int nsteps;
     long long nsamp0;           // correlator samples per chain before this launch
@@ -155,35 +176,47 @@ struct __align__(16) SlotRec {
     int s;
 };
 
+// One bead position in the per-warp shared position table.
+template <typename T>
+struct __align__(16) Pos {
+    T x, y, z, w;
+};
+
 // correlator levels kept in registers (levels 0..kRegLevels)
 #ifndef SS_REG_LEVELS
 #define SS_REG_LEVELS 2
 #endif
 constexpr int kRegLevels = SS_REG_LEVELS;
 
-// resident CTAs of 256 threads per SM the chunk kernel is compiled for
+// threads per CTA of the chunk kernel, and resident CTAs per SM it is compiled for
+constexpr int kChunkThreads = 128;
 #ifndef SS_CTAS_PER_SM
-#define SS_CTAS_PER_SM 3
+#define SS_CTAS_PER_SM 6
+#endif
+#ifndef SS_CTAS_PER_SM_MULTI
+#define SS_CTAS_PER_SM_MULTI 4  // for layouts with several beads per lane
 #endif
 
 // shared memory carve-up (bytes), identical on host and device
 struct SmemPlan {
-    int off_tab, off_log, off_corr, off_red, total;
+    int off_tab, off_pos, off_msk, off_log, off_corr, off_red, total;
 };
 
 template <typename T>
-__host__ __device__ inline SmemPlan smem_plan(int warps, int W, int Lsm, int nlog_chunk) {
+__host__ __device__ inline SmemPlan smem_plan(int warps, int W, int B, int Lsm, int nlog_chunk) {
     const int chains = warps * (32 / W);
     SmemPlan p;
     p.off_tab = 0;
-    int sz = warps * 32 * (int)sizeof(SlotRec<T>);
+    int sz = warps * 32 * B * (int)sizeof(SlotRec<T>);
+    p.off_pos = (sz + 15) & ~15;
+    sz = p.off_pos + warps * 32 * B * (int)sizeof(Pos<T>);
+    p.off_msk = (sz + 15) & ~15;
+    sz = p.off_msk + warps * 32 * B * (int)sizeof(unsigned long long);
     p.off_log = (sz + 15) & ~15;
     sz = p.off_log + nlog_chunk * 14 * (int)sizeof(double);
     p.off_corr = (sz + 15) & ~15;
     sz = p.off_corr + chains * Lsm * 2 * 3 * kCells * (int)sizeof(T);
-    p.off_red = (sz + 15) & ~15;
-    sz = p.off_red + chains * 3 * kCells * (int)sizeof(T);
-    p.total = (sz + 15) & ~15;
+    p.off_red = p.total = (sz + 15) & ~15;
     return p;
 }
 
@@ -247,6 +280,23 @@ __device__ __forceinline__ T hop_prob(const StepConst<T>& c, T d_new, T d_old) {
     return w < T(0.5) ? w : T(0.5);
 }
 
+// FP32 form of the same probability: e^{2y} = 2^t with t = c2 (d_new - d_old)
+// (c2 = 2 chop log2 e) by ex2.approx, 2/(1+e^{2y}) by rcp.approx.  t is capped
+// at 80 log2 e (y <= 40), where the probability is still a normal float; below
+// y = -40 the expression already equals its limit 2 pref.
+template <typename T>
+__device__ __forceinline__ T hop_prob_fast(const StepConst<T>& c, T d_new, T d_old) {
+    return hop_prob<T>(c, d_new, d_old);
+}
+template <>
+__device__ __forceinline__ float hop_prob_fast<float>(const StepConst<float>& c, float d_new, float d_old) {
+    const float t = fminf(c.c2 * (d_new - d_old), 115.41560327111707f);
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(t));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+    return fminf(c.two_pref * r, 0.5f);
+}
+
 // One multiple-tau level update of the lane's CPL cells.  hprev holds the
 // (already updated) cells of the level below; the new sample of this level is
 // the mean of the two newest samples below (its lag-0 and lag-1 cells), which
@@ -273,12 +323,17 @@ __device__ __forceinline__ void corr_level_from_below(const T (&hprev)[3][CPL], 
 }
 
 // ---------------------------------------------------------- chunk kernel ----
-template <typename T, int W>
-__global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
+// W lanes per chain, B beads per lane: bead i and slot i of a chain live on
+// lane i % W as its sub-slot i / W (NP = W*B >= N beads and slots).
+template <typename T, int W, int B>
+__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_MULTI)
+    chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
     constexpr int SEGS = 32 / W;
+    constexpr int NP = W * B;
     constexpr int CPL = kCells / W;  // correlator cells per lane
     constexpr int LR = kRegLevels;
     constexpr int G8 = W / 8;        // lanes per value group after seg_reduce8
+    using Mask = unsigned long long;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -291,29 +346,40 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
     const int mm = live ? m : 0;
     const uint32_t chain_id = a.chain_base + (uint32_t)mm;
     const int N = a.N;
-    const bool is_bead = ll < N;
     const unsigned segmask = (W == 32) ? kFull : (((1u << W) - 1u) << (seg * W));
-    const unsigned lanemask_lt = (1u << lane) - 1u;
+    const unsigned lt = ((1u << lane) - 1u) & segmask;  // lanes of this segment below this one
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemPlan plan = smem_plan<T>(nwarps, W, a.Lsm, a.nlog_chunk);
-    SlotRec<T>* tab = reinterpret_cast<SlotRec<T>*>(smem + plan.off_tab) + warp * 32 + seg * W;
+    const SmemPlan plan = smem_plan<T>(nwarps, W, B, a.Lsm, a.nlog_chunk);
+    SlotRec<T>* tab = reinterpret_cast<SlotRec<T>*>(smem + plan.off_tab) + (warp * SEGS + seg) * NP;
+    Pos<T>* pos = reinterpret_cast<Pos<T>*>(smem + plan.off_pos) + (warp * SEGS + seg) * NP;
+    Mask* msk = reinterpret_cast<Mask*>(smem + plan.off_msk) + (warp * SEGS + seg) * NP;
     double* slog = reinterpret_cast<double*>(smem + plan.off_log);
     T* scorr = reinterpret_cast<T*>(smem + plan.off_corr);
-    T* sred = reinterpret_cast<T*>(smem + plan.off_red);
 
     for (int i = threadIdx.x; i < a.nlog_chunk * 14; i += blockDim.x) slog[i] = 0.0;
 
     // ---- load state
     const T* Rg = static_cast<const T*>(a.R);
     const T* Ag = static_cast<const T*>(a.A);
-    T R[3], A[3];
+    T R[B][3], A[B][3];
+    int S[B];
     int Z = live ? a.Z[mm] : 0;
-    int S = (live && ll < Z) ? a.S[(size_t)mm * W + ll] : 0;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        R[d] = (live && is_bead) ? Rg[((size_t)mm * 3 + d) * W + ll] : T(0);
-        A[d] = (live && ll < Z) ? Ag[((size_t)mm * 3 + d) * W + ll] : T(0);
+    for (int b = 0; b < B; ++b) {
+        const int i = ll + b * W;
+        S[b] = (live && i < Z) ? a.S[(size_t)mm * NP + i] : 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            R[b][d] = (live && i < N) ? Rg[((size_t)mm * 3 + d) * NP + i] : T(0);
+            A[b][d] = (live && i < Z) ? Ag[((size_t)mm * 3 + d) * NP + i] : T(0);
+        }
+        Pos<T> p0;
+        p0.x = R[b][0];
+        p0.y = R[b][1];
+        p0.z = R[b][2];
+        p0.w = T(0);
+        pos[i] = p0;
     }
 
     // ---- correlator: levels 0..LR in registers, LR+1..LR+Lsm in shared
@@ -348,7 +414,10 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
                 }
         }
     }
-    __syncthreads();
+    if (a.nlog_chunk > 0)
+        __syncthreads();  // the CTA's stress-log buffer is zeroed
+    else
+        __syncwarp();
 
     // ---- flow schedule and periodic events, as step offsets in this launch
     const int never = 0x7fffffff;
@@ -386,96 +455,149 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
             }
             next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
         }
-        // ---- slot table for this step's force loop
-        {
+        // ---- slot table and per-bead slot masks for this step's spring forces
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
             SlotRec<T> rec;
-            rec.x = A[0];
-            rec.y = A[1];
-            rec.z = A[2];
-            rec.s = ll < Z ? S : -1;
-            tab[ll] = rec;
+            rec.x = A[b][0];
+            rec.y = A[b][1];
+            rec.z = A[b][2];
+            rec.s = i < Z ? S[b] : -1;
+            tab[i] = rec;
+            msk[i] = 0ull;
         }
-        // ---- random numbers of this step: block (ll, t, STEP, chain)
-        const uint4 w = philox4x32_10((uint32_t)ll, t, kPurposeStep, chain_id, a.key0, a.key1);
-        T nrm[4];
-        box_muller<T>(w.x, w.y, nrm[0], nrm[1]);
-        box_muller<T>(w.z, w.w, nrm[2], nrm[3]);
-        const T u = uniform_lo24<T>(w);
+        // ---- random numbers of this step: block (i, t, STEP, chain) per bead/slot i
+        T nrm[B][4], u[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const uint4 w = philox4x32_10_rk((uint32_t)(ll + b * W), t, kPurposeStep, chain_id, c.rk0, c.rk1);
+            box_muller<T>(w.x, w.y, nrm[b][0], nrm[b][1]);
+            box_muller<T>(w.z, w.w, nrm[b][2], nrm[b][3]);
+            u[b] = uniform_lo24<T>(w);
+        }
         __syncwarp();
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+            if (i < Z) atomicOr(&msk[S[b]], 1ull << i);
+        }
 
         // ---- substep 1: forces at time t, Euler-Maruyama, anchor advection
-        T F[3];
+        T F[B][3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const T Rl = __shfl_up_sync(kFull, R[d], 1, W);
-            const T Rr = __shfl_down_sync(kFull, R[d], 1, W);
-            T f = T(0);
-            if (ll > 0) f += c.k_b * (Rl - R[d]);
-            if (ll < N - 1) f += c.k_b * (Rr - R[d]);
-            F[d] = f;
-        }
-        {
-            // springs on this bead: k_s (sum_j A_j - n R), read in slot order
-            const int zloop = (__reduce_max_sync(kFull, (unsigned)Z) + 3) & ~3;
-            T sx = T(0), sy = T(0), sz = T(0), cnt = T(0);
-            for (int j = 0; j < zloop; j += 4) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const SlotRec<T> r = tab[j + q];
-                    if (r.s == ll) {
-                        sx += r.x;
-                        sy += r.y;
-                        sz += r.z;
-                        cnt += T(1);
-                    }
-                }
-            }
-            F[0] += c.k_s * (sx - cnt * R[0]);
-            F[1] += c.k_s * (sy - cnt * R[1]);
-            F[2] += c.k_s * (sz - cnt * R[2]);
-        }
-        T Rn[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            T flow = T(0);
-            if (kap_nz) flow = kap[3 * d] * R[0] + kap[3 * d + 1] * R[1] + kap[3 * d + 2] * R[2];
-            Rn[d] = is_bead ? (R[d] + c.mob * F[d] + c.dt * flow + c.amp * nrm[d]) : T(0);
-        }
-        if (kap_nz && ll < Z) {
-            T An[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                An[d] = A[d] + c.dt * (kap[3 * d] * A[0] + kap[3 * d + 1] * A[1] + kap[3 * d + 2] * A[2]);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) A[d] = An[d];
-        }
-
-        // ---- substep 2: hops on the new positions, one uniform per spring
-        {
-            const int si = (ll < Z) ? S : 0;
-            const int sm = si > 0 ? si - 1 : 0;
-            const int sp = si < N - 1 ? si + 1 : N - 1;
-            T d0 = T(0), dp = T(0), dm = T(0);
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+            const Pos<T> pl = pos[i > 0 ? i - 1 : 0];
+            const Pos<T> pr = pos[i < N - 1 ? i + 1 : i];
+            const T Rl[3] = {pl.x, pl.y, pl.z}, Rr[3] = {pr.x, pr.y, pr.z};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const T r0 = shfl(Rn[d], si, W) - A[d];
-                const T rp = shfl(Rn[d], sp, W) - A[d];
-                const T rm = shfl(Rn[d], sm, W) - A[d];
-                d0 += r0 * r0;
-                dp += rp * rp;
-                dm += rm * rm;
+                T f = T(0);
+                if (i > 0) f += c.k_b * (Rl[d] - R[b][d]);
+                if (i < N - 1) f += c.k_b * (Rr[d] - R[b][d]);
+                F[b][d] = f;
             }
-            if (ll < Z) {
-                const T pp = (si < N - 1) ? hop_prob<T>(c, dp, d0) : T(0);
-                const T pm = (si > 0) ? hop_prob<T>(c, dm, d0) : T(0);
-                if (u < pp) {
-                    S = si + 1;
-                    ++cnt_up;
-                } else if (u < pp + pm) {
-                    S = si - 1;
-                    ++cnt_dn;
+        }
+        __syncwarp();
+        bool more = false;
+        Mask mrest[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            // springs on this bead: k_s (sum_j A_j - n R), slots in ascending order
+            Mask mb = msk[ll + b * W];
+            T sx = T(0), sy = T(0), sz = T(0), cnt = T(0);
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const bool has = mb != 0ull;
+                const SlotRec<T> r = tab[has ? __ffsll((long long)mb) - 1 : 0];
+                mb &= mb - 1ull;
+                sx += has ? r.x : T(0);
+                sy += has ? r.y : T(0);
+                sz += has ? r.z : T(0);
+                cnt += has ? T(1) : T(0);
+            }
+            mrest[b] = mb;
+            more |= mb != 0ull;
+            F[b][0] += c.k_s * (sx - cnt * R[b][0]);
+            F[b][1] += c.k_s * (sy - cnt * R[b][1]);
+            F[b][2] += c.k_s * (sz - cnt * R[b][2]);
+        }
+        if (__any_sync(kFull, more)) {  // a third spring on one bead: rare
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                // the first two slots were added already; add the rest in order
+                Mask mb = mrest[b];
+                T sx = T(0), sy = T(0), sz = T(0), cnt = T(0);
+                while (mb) {
+                    const SlotRec<T> r = tab[__ffsll((long long)mb) - 1];
+                    mb &= mb - 1ull;
+                    sx += r.x;
+                    sy += r.y;
+                    sz += r.z;
+                    cnt += T(1);
                 }
+                F[b][0] += c.k_s * (sx - cnt * R[b][0]);
+                F[b][1] += c.k_s * (sy - cnt * R[b][1]);
+                F[b][2] += c.k_s * (sz - cnt * R[b][2]);
             }
+        }
+        T Rn[B][3];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                T flow = T(0);
+                if (kap_nz) flow = kap[3 * d] * R[b][0] + kap[3 * d + 1] * R[b][1] + kap[3 * d + 2] * R[b][2];
+                Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d]) : T(0);
+            }
+            if (kap_nz && i < Z) {
+                T An[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    An[d] = A[b][d] + c.dt * (kap[3 * d] * A[b][0] + kap[3 * d + 1] * A[b][1] + kap[3 * d + 2] * A[b][2]);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) A[b][d] = An[d];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            Pos<T> pn;
+            pn.x = Rn[b][0];
+            pn.y = Rn[b][1];
+            pn.z = Rn[b][2];
+            pn.w = T(0);
+            pos[ll + b * W] = pn;
+        }
+        __syncwarp();
+
+        // ---- substep 2: hops on the new positions, one uniform per spring;
+        // sub-slots above every chain's Z in this warp are skipped
+        const int zw = (int)__reduce_max_sync(kFull, (unsigned)Z);
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (b * W >= zw) break;
+            const int i = ll + b * W;
+            const bool occ = i < Z;
+            const int si = occ ? S[b] : 0;
+            const int sm = si > 0 ? si - 1 : 0;
+            const int sp = si < N - 1 ? si + 1 : N - 1;
+            const Pos<T> q0 = pos[si], qp = pos[sp], qm = pos[sm];
+            const T r0[3] = {q0.x - A[b][0], q0.y - A[b][1], q0.z - A[b][2]};
+            const T rp[3] = {qp.x - A[b][0], qp.y - A[b][1], qp.z - A[b][2]};
+            const T rm[3] = {qm.x - A[b][0], qm.y - A[b][1], qm.z - A[b][2]};
+            const T d0 = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2];
+            const T dp = rp[0] * rp[0] + rp[1] * rp[1] + rp[2] * rp[2];
+            const T dm = rm[0] * rm[0] + rm[1] * rm[1] + rm[2] * rm[2];
+            const T pp = (si < N - 1) ? hop_prob_fast<T>(c, dp, d0) : T(0);
+            const T pm = (si > 0) ? hop_prob_fast<T>(c, dm, d0) : T(0);
+            const bool up = occ && (u[b] < pp);
+            const bool dn = occ && !up && (u[b] < pp + pm);
+            S[b] = up ? si + 1 : (dn ? si - 1 : S[b]);
+            cnt_up += up ? 1u : 0u;
+            cnt_dn += dn ? 1u : 0u;
         }
 
         // ---- substep 3a: creation, K attempts at both ends
@@ -484,81 +606,108 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
         if (Zc < a.zmax) last = (a.create_mode == 0) ? a.zmax : Zc + 1;
         if (Zc >= a.zmax && a.create_mode == 1 && ll == 0 && live) ++cnt_drop;
         const int K = last - first;
-        int end_new = -1;
-        if (ll >= first && ll < last) {
-            const T pc = c.pc[K];
-            if (u < pc)
-                end_new = 0;
-            else if (u < T(2) * pc)
-                end_new = N - 1;
+        const T pc = c.pc[K];
+        int end_new[B];
+        bool any_new = false;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+            const bool att = (i >= first) && (i < last);
+            end_new[b] = !att ? -1 : (u[b] < pc ? 0 : (u[b] < T(2) * pc ? N - 1 : -1));
+            any_new |= end_new[b] >= 0;
         }
-        T Anew[3] = {T(0), T(0), T(0)};
-        const unsigned cre_any = __ballot_sync(kFull, end_new >= 0);
-        if (cre_any) {
-            T e0[3], eN[3];
+        T Anew[B][3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                e0[d] = shfl(Rn[d], 0, W);
-                eN[d] = shfl(Rn[d], N - 1, W);
-            }
-            if (end_new >= 0) {
-                const uint4 wc = philox4x32_10((uint32_t)ll, t, kPurposeCreate, chain_id, a.key0, a.key1);
-                T n3[4];
-                box_muller<T>(wc.x, wc.y, n3[0], n3[1]);
-                box_muller<T>(wc.z, wc.w, n3[2], n3[3]);
+        for (int b = 0; b < B; ++b) Anew[b][0] = Anew[b][1] = Anew[b][2] = T(0);
+        if (__any_sync(kFull, any_new)) {
 #pragma unroll
-                for (int d = 0; d < 3; ++d) Anew[d] = (end_new == 0 ? e0[d] : eN[d]) + c.sa * n3[d];
-                ++cnt_cr;
+            for (int b = 0; b < B; ++b) {
+                if (end_new[b] >= 0) {
+                    const Pos<T> pe = pos[end_new[b]];
+                    const uint4 wc = philox4x32_10_rk((uint32_t)(ll + b * W), t, kPurposeCreate, chain_id, c.rk0,
+                                                      c.rk1);
+                    T n3[4];
+                    box_muller<T>(wc.x, wc.y, n3[0], n3[1]);
+                    box_muller<T>(wc.z, wc.w, n3[2], n3[3]);
+                    Anew[b][0] = pe.x + c.sa * n3[0];
+                    Anew[b][1] = pe.y + c.sa * n3[1];
+                    Anew[b][2] = pe.z + c.sa * n3[2];
+                    ++cnt_cr;
+                }
             }
         }
 
         // ---- substep 3b: destruction at the ends, then re-indexing
-        bool alive_old = ll < Zc;
-        if (ll < Zc && (S == 0 || S == N - 1) && nrm[3] < c.cd) {
-            alive_old = false;
-            ++cnt_de;
+        bool alive_old[B], alive_new[B];
+        bool any_change = false;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+            const bool hit = nrm[b][3] < c.cd;
+            const bool kill_old = (i < Zc) && (S[b] == 0 || S[b] == N - 1) && hit;
+            const bool kill_new = (end_new[b] >= 0) && a.destroy_new && hit;
+            alive_old[b] = (i < Zc) && !kill_old;
+            alive_new[b] = (end_new[b] >= 0) && !kill_new;
+            cnt_de += (kill_old ? 1u : 0u) + (kill_new ? 1u : 0u);
+            any_change |= kill_old || (end_new[b] >= 0);
         }
-        bool alive_new = end_new >= 0;
-        if (alive_new && a.destroy_new && nrm[3] < c.cd) {
-            alive_new = false;
-            ++cnt_de;
-        }
-        const unsigned changed = __ballot_sync(kFull, (ll < Zc && !alive_old) || end_new >= 0);
-        if (changed) {
-            const unsigned keep = __ballot_sync(kFull, alive_old) & segmask;
-            const unsigned n1 = __ballot_sync(kFull, alive_new && end_new == 0) & segmask;
-            const unsigned nN = __ballot_sync(kFull, alive_new && end_new == N - 1) & segmask;
-            const int nk = __popc(keep), n1c = __popc(n1);
-            int dest = -1;
-            if (alive_old)
-                dest = __popc(keep & lanemask_lt);
-            else if (alive_new && end_new == 0)
-                dest = nk + __popc(n1 & lanemask_lt);
-            else if (alive_new)
-                dest = nk + n1c + __popc(nN & lanemask_lt);
+        if (__any_sync(kFull, any_change)) {
+            // slot order: sub-slot major, then lane; survivors, then new springs at
+            // bead 1 in attempt order, then new springs at bead N
+            int dest[B];
+            int base = 0;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const unsigned kb = __ballot_sync(kFull, alive_old[b]) & segmask;
+                dest[b] = alive_old[b] ? base + __popc(kb & lt) : -1;
+                base += __popc(kb);
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const bool e0 = alive_new[b] && end_new[b] == 0;
+                const unsigned nb = __ballot_sync(kFull, e0) & segmask;
+                if (e0) dest[b] = base + __popc(nb & lt);
+                base += __popc(nb);
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const bool eN = alive_new[b] && end_new[b] == N - 1;
+                const unsigned nb = __ballot_sync(kFull, eN) & segmask;
+                if (eN) dest[b] = base + __popc(nb & lt);
+                base += __popc(nb);
+            }
+            const int Znew = base;
             __syncwarp();
-            if (dest >= 0) {
-                SlotRec<T> rec;
-                rec.x = alive_old ? A[0] : Anew[0];
-                rec.y = alive_old ? A[1] : Anew[1];
-                rec.z = alive_old ? A[2] : Anew[2];
-                rec.s = alive_old ? S : end_new;
-                tab[dest] = rec;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                if (dest[b] >= 0) {
+                    SlotRec<T> rec;
+                    rec.x = alive_old[b] ? A[b][0] : Anew[b][0];
+                    rec.y = alive_old[b] ? A[b][1] : Anew[b][1];
+                    rec.z = alive_old[b] ? A[b][2] : Anew[b][2];
+                    rec.s = alive_old[b] ? S[b] : end_new[b];
+                    tab[dest[b]] = rec;
+                }
             }
             __syncwarp();
-            const int Znew = nk + n1c + __popc(nN);
-            if (ll < Znew) {
-                const SlotRec<T> rec = tab[ll];
-                S = rec.s;
-                A[0] = rec.x;
-                A[1] = rec.y;
-                A[2] = rec.z;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int i = ll + b * W;
+                if (i < Znew) {
+                    const SlotRec<T> rec = tab[i];
+                    S[b] = rec.s;
+                    A[b][0] = rec.x;
+                    A[b][1] = rec.y;
+                    A[b][2] = rec.z;
+                }
             }
             __syncwarp();
             Z = Znew;
         }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) R[d] = Rn[d];
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) R[b][d] = Rn[b][d];
 
         // ---- stress of the new state (Eq. stress_tensor_single_chain, App. B)
         const bool do_log = (s == next_log);
@@ -566,25 +715,35 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
         const bool do_rc = (s == next_rc) && kap_nz;
         if (s == next_rc) next_rc += a.recenter_every;
         if (corr_on || do_log) {
-            T q[3], dd[3];
-            const int si = (ll < Z) ? S : 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const T r1 = __shfl_down_sync(kFull, R[d], 1, W);
-                q[d] = (ll < N - 1) ? (r1 - R[d]) : T(0);
-                const T rs = shfl(R[d], si, W);
-                dd[d] = (ll < Z) ? (rs - A[d]) : T(0);
-            }
             // per-lane parts of sigma_ab (bonds) and sigma_ab + sigma^(v)_ab
-            T v[8];
-            v[0] = c.k_b * q[0] * q[1];
-            v[1] = c.k_b * q[0] * q[2];
-            v[2] = c.k_b * q[1] * q[2];
-            v[3] = v[0] + c.k_s * dd[0] * dd[1];
-            v[4] = v[1] + c.k_s * dd[0] * dd[2];
-            v[5] = v[2] + c.k_s * dd[1] * dd[2];
-            v[6] = T(0);
-            v[7] = T(0);
+            T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+            T dgp[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int i = ll + b * W;
+                const Pos<T> p1 = pos[i < N - 1 ? i + 1 : i];
+                const Pos<T> ps = pos[i < Z ? S[b] : 0];
+                T q[3] = {p1.x - R[b][0], p1.y - R[b][1], p1.z - R[b][2]};
+                T dd[3] = {ps.x - A[b][0], ps.y - A[b][1], ps.z - A[b][2]};
+                if (!(i < N - 1)) q[0] = q[1] = q[2] = T(0);
+                if (!(i < Z)) dd[0] = dd[1] = dd[2] = T(0);
+                const T kq0 = c.k_b * q[0], kq1 = c.k_b * q[1];
+                const T kd0 = c.k_s * dd[0], kd1 = c.k_s * dd[1];
+                v[0] += kq0 * q[1];
+                v[1] += kq0 * q[2];
+                v[2] += kq1 * q[2];
+                v[3] += kd0 * dd[1];
+                v[4] += kd0 * dd[2];
+                v[5] += kd1 * dd[2];
+                if (do_log) {
+                    dgp[0] += kq0 * q[0];
+                    dgp[1] += kq1 * q[1];
+                    dgp[2] += c.k_b * q[2] * q[2];
+                }
+            }
+            v[3] += v[0];
+            v[4] += v[1];
+            v[5] += v[2];
             const T red = seg_reduce8<T, W>(v, ll);
             T sig[3], tot[3];
 #pragma unroll
@@ -595,7 +754,7 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
             if (do_log) {
                 T dg[3];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) dg[d] = seg_sum<T, W>(c.k_b * q[d] * q[d]) - c.NkT;
+                for (int d = 0; d < 3; ++d) dg[d] = seg_sum<T, W>(dgp[d]) - c.NkT;
                 const int slot = log_slot++;
                 if (live && ll == 0 && slot < a.nlog_chunk) {
                     double* L = slog + slot * 14;
@@ -647,7 +806,7 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
                             ab = hb + 96;
                         } else {
                             hb = static_cast<T*>(a.histg) + ((size_t)mm * Lglob + (l - Lsave)) * 96;
-                            ab = static_cast<T*>(a.accg) + ((size_t)mm * Lglob + (l - Lsave)) * 96;
+                            ab = static_cast<T*>(a.accc) + ((size_t)mm * a.levels + l) * 96;
                         }
 #pragma unroll
                         for (int d = 0; d < 3; ++d)
@@ -675,15 +834,32 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
             }
         }
         if (do_rc) {
+            T csum[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) csum[d] += (ll + b * W < N) ? R[b][d] : T(0);
             T com[3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) com[d] = seg_sum<T, W>(is_bead ? R[d] : T(0)) / T(N);
+            for (int d = 0; d < 3; ++d) com[d] = seg_sum<T, W>(csum[d]) / T(N);
+            __syncwarp();
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (is_bead) R[d] -= com[d];
-                if (ll < Z) A[d] -= com[d];
+            for (int b = 0; b < B; ++b) {
+                const int i = ll + b * W;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (i < N) R[b][d] -= com[d];
+                    if (i < Z) A[b][d] -= com[d];
+                }
+                Pos<T> pn;
+                pn.x = R[b][0];
+                pn.y = R[b][1];
+                pn.z = R[b][2];
+                pn.w = T(0);
+                pos[i] = pn;
             }
         }
+        __syncwarp();
     }
 
     // ---- store state
@@ -692,14 +868,18 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
     bool bad = false;
     if (live) {
         if (ll == 0) a.Z[mm] = Z;
-        a.S[(size_t)mm * W + ll] = (ll < Z) ? S : -1;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (is_bead) {
-                Rw[((size_t)mm * 3 + d) * W + ll] = R[d];
-                bad |= !Mth<T>::finite(R[d]);
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+            a.S[(size_t)mm * NP + i] = (i < Z) ? S[b] : -1;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (i < N) {
+                    Rw[((size_t)mm * 3 + d) * NP + i] = R[b][d];
+                    bad |= !Mth<T>::finite(R[b][d]);
+                }
+                Aw[((size_t)mm * 3 + d) * NP + i] = (i < Z) ? A[b][d] : T(0);
             }
-            Aw[((size_t)mm * 3 + d) * W + ll] = (ll < Z) ? A[d] : T(0);
         }
     }
     if (__any_sync(kFull, bad) && lane == 0) {
@@ -719,58 +899,30 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
         }
     }
 
-    // ---- correlator: save the stored levels, flush this launch's sums per slice
-    if (corr_on) {
+    // ---- correlator: save the stored levels, store this launch's sums per chain
+    if (corr_on && live) {
         T* Hw = static_cast<T*>(a.hist);
-        if (live) {
+        T* C = static_cast<T*>(a.accc) + (size_t)mm * a.levels * 96;
 #pragma unroll
-            for (int l = 0; l <= LR; ++l) {
-                if (l >= a.levels) break;
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-#pragma unroll
-                    for (int k = 0; k < CPL; ++k)
-                        Hw[(((size_t)mm * Lsave + l) * 3 + d) * kCells + k * W + ll] = hr[l][d][k];
-            }
-            for (int l = 0; l < a.Lsm; ++l) {
-                const T* base = scorr + ((size_t)(cslot * a.Lsm + l) * 2) * 96;
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-#pragma unroll
-                    for (int k = 0; k < CPL; ++k)
-                        Hw[(((size_t)mm * Lsave + LR + 1 + l) * 3 + d) * kCells + k * W + ll] =
-                            base[d * kCells + k * W + ll];
-            }
-        }
-        // deterministic per-slice reduction, level by level
-        double* out = a.acc64 + (size_t)blockIdx.x * a.levels * 96;
-        for (int l = 0; l < a.levels; ++l) {
-            __syncthreads();
+        for (int l = 0; l <= LR; ++l) {
+            if (l >= a.levels) break;
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
-                    const int cell = k * W + ll;
-                    T v = T(0);
-                    if (l <= LR) {
-#pragma unroll
-                        for (int r = 0; r <= LR; ++r)
-                            if (r == l) v = ar[r][d][k];
-                    } else if (l < Lsave) {
-                        v = scorr[((size_t)(cslot * a.Lsm + (l - LR - 1)) * 2) * 96 + 96 + d * kCells + cell];
-                    } else {
-                        T* ab = static_cast<T*>(a.accg) + ((size_t)mm * Lglob + (l - Lsave)) * 96;
-                        v = live ? ab[d * kCells + cell] : T(0);
-                        if (live) ab[d * kCells + cell] = T(0);
-                    }
-                    sred[(size_t)cslot * 96 + d * kCells + cell] = live ? v : T(0);
+                    Hw[(((size_t)mm * Lsave + l) * 3 + d) * kCells + k * W + ll] = hr[l][d][k];
+                    C[(size_t)l * 96 + d * kCells + k * W + ll] = ar[l][d][k];
                 }
-            __syncthreads();
-            for (int i = threadIdx.x; i < 96; i += blockDim.x) {
-                double sum = 0.0;
-                for (int q = 0; q < cpc; ++q) sum += (double)sred[(size_t)q * 96 + i];
-                out[(size_t)l * 96 + i] += sum;
-            }
+        }
+        for (int l = 0; l < a.Lsm; ++l) {
+            const T* base = scorr + ((size_t)(cslot * a.Lsm + l) * 2) * 96;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) {
+                    Hw[(((size_t)mm * Lsave + LR + 1 + l) * 3 + d) * kCells + k * W + ll] = base[d * kCells + k * W + ll];
+                    C[(size_t)(LR + 1 + l) * 96 + d * kCells + k * W + ll] = base[96 + d * kCells + k * W + ll];
+                }
         }
     }
 
@@ -778,7 +930,8 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
     if (a.log_every > 0 && a.nlog_chunk > 0) {
         __syncthreads();
         const long long first_m = a.t0 / a.log_every + 1;  // first log multiple in or after t0+1
-        const int grp = (int)(((long long)blockIdx.x * a.groups) / a.slices);
+        const int slice = (int)(((long long)blockIdx.x * cpc) / kSliceChains);
+        const int grp = (int)(((long long)slice * a.groups) / a.slices);
         for (int i = threadIdx.x; i < a.nlog_chunk * 14; i += blockDim.x) {
             const int slot = i / 14, k = i % 14;
             const long long idx = first_m + slot - a.log_m0 - 1;
@@ -789,12 +942,32 @@ __global__ void __launch_bounds__(256, SS_CTAS_PER_SM) chunk_kernel(const ChunkA
     }
 }
 
+// ---------------------------------------------------------- reduce kernel ----
+// Folds the chains' correlator sums of one launch into FP64 slice sums:
+// acc64[s][l][i] += sum over the chains of slice s, in chain order, of
+// accc[m][l][i]; accc is zeroed for the next launch.  Levels without a new
+// sample in the launch are skipped (their sums are zero).  Grid: (slices, L).
+template <typename T>
+__global__ void corr_reduce_kernel(T* __restrict__ accc, double* __restrict__ acc64, int M, int L,
+                                   int slice_chains, unsigned long long level_mask) {
+    const int sl = blockIdx.x, l = blockIdx.y, i = threadIdx.x;
+    if (i >= 96 || !((level_mask >> l) & 1ull)) return;
+    const int m0 = sl * slice_chains, m1 = min(M, m0 + slice_chains);
+    double sum = 0.0;
+    for (int m = m0; m < m1; ++m) {
+        T* p = accc + ((size_t)m * L + l) * 96 + i;
+        sum += (double)*p;
+        *p = T(0);
+    }
+    acc64[((size_t)sl * L + l) * 96 + i] += sum;
+}
+
 // ------------------------------------------------------------ init kernel ----
 // Equilibrium initial state (Sec. 3.1 sampling): ideal-chain bonds with
 // variance kT/k_b per component, Z ~ Poisson(N/N0) by inverse CDF on a 53-bit
 // uniform (capped at z_max), S uniform on the beads, anchors Gaussian around
 // their bead with variance kT/k_s.  One thread per chain, FP64 arithmetic.
-template <typename T, int W>
+template <typename T, int NP>
 __global__ void init_kernel(T* R, T* A, int32_t* S, int32_t* Z, int M, int N, int zmax, double sb,
                             double sa, double lam, uint32_t key0, uint32_t key1, uint32_t chain_base) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -809,8 +982,8 @@ __global__ void init_kernel(T* R, T* A, int32_t* S, int32_t* Z, int M, int N, in
         box_muller<double>(w.z, w.w, n[2], n[3]);
         for (int d = 0; d < 3; ++d) r[i + 1][d] = r[i][d] + sb * n[d];
     }
-    for (int i = 0; i < W; ++i)
-        for (int d = 0; d < 3; ++d) R[((size_t)m * 3 + d) * W + i] = i < N ? T(r[i][d]) : T(0);
+    for (int i = 0; i < NP; ++i)
+        for (int d = 0; d < 3; ++d) R[((size_t)m * 3 + d) * NP + i] = i < N ? T(r[i][d]) : T(0);
     int z = zmax;
     {
         const uint4 w = philox4x32_10(0u, 0u, kPurposeInitZ, cid, key0, key1);
@@ -826,7 +999,7 @@ __global__ void init_kernel(T* R, T* A, int32_t* S, int32_t* Z, int M, int N, in
         }
     }
     Z[m] = z;
-    for (int j = 0; j < W; ++j) {
+    for (int j = 0; j < NP; ++j) {
         int sj = -1;
         double an[3] = {0.0, 0.0, 0.0};
         if (j < z) {
@@ -838,8 +1011,8 @@ __global__ void init_kernel(T* R, T* A, int32_t* S, int32_t* Z, int M, int N, in
             box_muller<double>(wa.z, wa.w, n[2], n[3]);
             for (int d = 0; d < 3; ++d) an[d] = r[sj][d] + sa * n[d];
         }
-        S[(size_t)m * W + j] = sj;
-        for (int d = 0; d < 3; ++d) A[((size_t)m * 3 + d) * W + j] = T(an[d]);
+        S[(size_t)m * NP + j] = sj;
+        for (int d = 0; d < 3; ++d) A[((size_t)m * 3 + d) * NP + j] = T(an[d]);
     }
 }
 

@@ -144,7 +144,7 @@ def test_fp64_parity_workload_bit_exact_integers():
 
 
 @pytest.mark.parametrize("case", ["N2", "zmax1", "no_springs", "cpu_mode", "destroy_new", "M1",
-                                  "ragged", "fast_create"])
+                                  "ragged", "fast_create", "N48", "N64", "N33_crowded"])
 def test_fp64_edge_cases(case):
     kw = dict(N=16)
     M = 37
@@ -165,6 +165,12 @@ def test_fp64_edge_cases(case):
         M = 8 * 3 + 5  # 8 chains per CTA at N > 16: a partial last CTA
     elif case == "fast_create":
         kw = dict(N=6, N0=0.05, zeta_s=0.02)  # creation capped at 1/2 per attempt
+    elif case == "N48":
+        kw = dict(N=48)  # three beads per lane
+    elif case == "N64":
+        kw = dict(N=64, N0=2.0)  # four beads per lane, up to 64 springs
+    elif case == "N33_crowded":
+        kw = dict(N=33, N0=0.6)  # sub-slots beyond the first 16 are occupied
     p = Params(**kw)
     _fp64_stepwise(p, M, seed=17, steps_each=1, blocks=150)
 
@@ -204,7 +210,7 @@ def _first_tie(margins):
     return first
 
 
-@pytest.mark.parametrize("N,kappa", [(32, None), (16, None), (24, 0.05)])
+@pytest.mark.parametrize("N,kappa", [(32, None), (16, None), (24, 0.05), (48, None)])
 def test_fp32_stepwise_parity_until_near_tie(N, kappa):
     p = Params(N=N)
     M = 512 if N > 16 else 1024
