@@ -163,7 +163,7 @@ def run_ours(args):
         g.run(spc)
     torch.cuda.synchronize()
     c0 = g.counters()["launches"]
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    g.kernel_timing(True)
     clocks = ClockSampler(local)
     clocks.start()
     _barrier(ws)
@@ -172,21 +172,20 @@ def run_ours(args):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for k in range(args.steps):
-        ev[k][0].record(stream)
         g.run(spc)
-        ev[k][1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
     _barrier(ws)
     clk = clocks.stop()
     ms_total = t0.elapsed_time(t1)
     launches = g.counters()["launches"] - c0
-    per_call_ms = [a.elapsed_time(b) for a, b in ev]
+    chain_ms, chain_launches = g.kernel_time()  # CUDA events around each chain-kernel launch
+    g.kernel_timing(False)
     ms_total = _max_over_ranks(ms_total, ws)
     bead_steps = float(M) * N * spc * args.steps
     value = bead_steps * ws / (ms_total / 1e3)
-    kernel_ms = sum(per_call_ms) / max(launches, 1)  # one kernel type runs in the region
-    steps_per_launch = spc * args.steps / max(launches, 1)
+    kernel_ms = chain_ms / max(chain_launches, 1)
+    steps_per_launch = spc * args.steps / max(chain_launches, 1)
     alg_ops_launch = ALG_OPS_PER_BEAD_STEP * M * N * steps_per_launch
     achieved = alg_ops_launch / (kernel_ms / 1e3)
     peak = SMS * LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6
@@ -257,7 +256,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-ops/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "chunk_kernel<float,32>", "kernel_ms": kernel_ms,
+                     "kernel": "chunk_kernel<float,16,2>", "kernel_ms": kernel_ms,
+                     "kernel_share_of_region": chain_ms / ms_total if ws == 1 else None,
                      "alg_ops_per_bead_step": ALG_OPS_PER_BEAD_STEP,
                      "peak_basis": "152 SMs x 128 lanes x 2070 MHz (nominal max clock), 1 lane-op/lane/clock"},
         "clocks": clk,
@@ -293,7 +293,7 @@ def run_reference(args):
     vals = []
     cb = None
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(args.cpu_chains, max(50, args.cpu_steps // 10))
+        cb = cpu_baseline(args.cpu_chains, max(50, args.cpu_steps // 5))
         if k >= args.warmup:
             vals.append(cb["value"])
     value = float(np.mean(vals))
@@ -316,8 +316,8 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=2048)
     ap.add_argument("--chunk", type=int, default=1024)
     ap.add_argument("--plain-steps", type=int, default=200)
-    ap.add_argument("--cpu-chains", type=int, default=2048)
-    ap.add_argument("--cpu-steps", type=int, default=3000)
+    ap.add_argument("--cpu-chains", type=int, default=4096)
+    ap.add_argument("--cpu-steps", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

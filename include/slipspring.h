@@ -192,6 +192,14 @@ int ss_status(ss_ctx* ctx, int32_t* status);
 /* Wait for the context's stream. */
 int ss_synchronize(ss_ctx* ctx);
 
+/* Kernel timing (support for benchmarks; not in the paper).  While enabled
+ * (enable = 1), every launch of the chain kernel is bracketed by CUDA events on
+ * the context's stream.  ss_kernel_time synchronises and returns the summed
+ * event time of those launches and their number, then clears them.
+ * enable = 0 stops recording. */
+int ss_kernel_timing(ss_ctx* ctx, int enable);
+int ss_kernel_time(ss_ctx* ctx, double* chain_kernel_ms, int64_t* chain_launches);
+
 /* ---- allocation-free run ---------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot
  * call cudaMalloc: code that runs while a CUDA graph is being captured, code

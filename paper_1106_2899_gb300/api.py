@@ -160,6 +160,17 @@ class SlipSpring:
         return dict(zip(["hops_up", "hops_down", "created", "destroyed", "dropped", "launches",
                          "nonfinite"], out.tolist()))
 
+    def kernel_timing(self, enable=True):
+        """Bracket each chain-kernel launch with CUDA events (benchmark support)."""
+        self._chk(self.lib.ss_kernel_timing(self.h, 1 if enable else 0), "ss_kernel_timing")
+
+    def kernel_time(self):
+        """(summed chain-kernel milliseconds, launches) since timing was enabled."""
+        ms = C.c_double()
+        n = C.c_int64()
+        self._chk(self.lib.ss_kernel_time(self.h, C.byref(ms), C.byref(n)), "ss_kernel_time")
+        return ms.value, n.value
+
     def status(self):
         s = C.c_int32()
         self._chk(self.lib.ss_status(self.h, C.byref(s)), "ss_status")

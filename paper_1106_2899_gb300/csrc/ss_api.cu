@@ -64,6 +64,8 @@ struct ss_ctx {
     unsigned long long* counters = nullptr;  // [8]
     int32_t* status = nullptr;
     long long launches = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // chain-kernel launches while timing
     std::string err;
 };
 
@@ -233,8 +235,18 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     }
     const ssk::StepConst<T> sc = step_const<T>(c, e.N);
     const int ctas = (e.M + chains_per_cta(W) - 1) / chains_per_cta(W);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (c->timing) {
+        SS_CUDA(c, cudaEventCreate(&ev0));
+        SS_CUDA(c, cudaEventCreate(&ev1));
+        SS_CUDA(c, cudaEventRecord(ev0, c->stream));
+    }
     ssk::chunk_kernel<T, W, B><<<ctas, kThreads, plan.total, c->stream>>>(a, sc);
     SS_CUDA(c, cudaGetLastError());
+    if (c->timing) {
+        SS_CUDA(c, cudaEventRecord(ev1, c->stream));
+        c->events.emplace_back(ev0, ev1);
+    }
     c->launches++;
     if (c->levels > 0) {
         const unsigned long long mask = new_sample_levels(c->nsamp, nsteps, c->levels);
@@ -667,6 +679,10 @@ int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double
 int ss_destroy(ss_ctx* c) {
     if (!c) return SS_OK;
     if (c->stream || c->counters) cudaStreamSynchronize(c->stream);
+    for (auto& pr : c->events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
     for (Elem& e : c->el) free_elem(e);
     if (c->counters) cudaFree(c->counters);
     if (c->status) cudaFree(c->status);
@@ -780,6 +796,31 @@ int ss_status(ss_ctx* c, int32_t* status) {
 int ss_synchronize(ss_ctx* c) {
     if (!c) return SS_EINVAL;
     SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SS_OK;
+}
+
+int ss_kernel_timing(ss_ctx* c, int enable) {
+    if (!c) return SS_EINVAL;
+    c->timing = enable != 0;
+    return SS_OK;
+}
+
+int ss_kernel_time(ss_ctx* c, double* chain_kernel_ms, int64_t* chain_launches) {
+    if (!c) return SS_EINVAL;
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    double total = 0.0;
+    for (auto& pr : c->events) {
+        float ms = 0.0f;
+        SS_CUDA(c, cudaEventElapsedTime(&ms, pr.first, pr.second));
+        total += ms;
+    }
+    if (chain_kernel_ms) *chain_kernel_ms = total;
+    if (chain_launches) *chain_launches = (int64_t)c->events.size();
+    for (auto& pr : c->events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    c->events.clear();
     return SS_OK;
 }
 
