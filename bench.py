@@ -151,8 +151,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def make(chunk):
-        # rank r runs its own 65536 chains (global chain ids r*M ...): weak scaling
-        g = SlipSpring([(M, N)], precision="fp32", seed=w["seed"] + 1000 * rank, stream=stream.cuda_stream)
+        # rank r runs its own M chains, global chain ids r*M .. r*M+M-1 (weak scaling)
+        g = SlipSpring([(M, N)], precision="fp32", seed=w["seed"], stream=stream.cuda_stream, chain_offset=rank * M)
         g.set_params(**synth.PAPER, corr_levels=w["levels"], groups=32, chunk_steps=chunk)
         return g
 

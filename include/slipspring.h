@@ -160,6 +160,13 @@ int ss_get_state(ss_ctx* ctx, int elem, double* R, int32_t* Z, int32_t* S, doubl
 int ss_set_state(ss_ctx* ctx, int elem, const double* R, const int32_t* Z, const int32_t* S,
                  const double* A);
 
+/* Global chain id of chain 0 of element 0 (default 0); the elements follow
+ * contiguously.  A shard of a larger ensemble (one GPU or process of several)
+ * passes the start of its contiguous chain range, so that every chain draws
+ * the same Philox numbers whatever the number of shards.  Errors: SS_EINVAL if
+ * offset + total chains passes 2^32. */
+int ss_set_chain_offset(ss_ctx* ctx, uint32_t offset);
+
 /* Steps taken so far. */
 int ss_step_count(ss_ctx* ctx, int64_t* steps);
 

@@ -19,7 +19,8 @@ SS_CH_AUTO, SS_CH_CROSS, SS_CH_TOTAL = 0, 1, 2
 EXPORTS = ["ss_create", "ss_set_params", "ss_set_flow", "ss_run", "ss_stress", "ss_correlator",
            "ss_destroy", "ss_last_error", "ss_get_state", "ss_set_state", "ss_step_count",
            "ss_reset_observables", "ss_corr_sums", "ss_log_sums", "ss_counters", "ss_status",
-           "ss_synchronize", "ss_run_noalloc", "ss_kernel_timing", "ss_kernel_time"]
+           "ss_synchronize", "ss_run_noalloc", "ss_kernel_timing", "ss_kernel_time",
+           "ss_set_chain_offset"]
 
 
 class ss_element(C.Structure):
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
         "ss_status": [vp, i32p],
         "ss_synchronize": [vp],
         "ss_kernel_timing": [vp, C.c_int],
+        "ss_set_chain_offset": [vp, C.c_uint32],
         "ss_kernel_time": [vp, dp, i64p],
         "ss_run_noalloc": [P(ss_params), C.c_int, C.c_uint64, C.c_int32, C.c_int32, C.c_uint32, C.c_int64,
                            C.c_int64, dp, vp, vp, vp, vp, vp, vp, vp],

@@ -24,7 +24,7 @@ def _p(a, ctype):
 class SlipSpring:
     """A context of one or more elements (ensembles of equal-length chains)."""
 
-    def __init__(self, elements, precision="fp32", seed=0, stream=None):
+    def __init__(self, elements, precision="fp32", seed=0, stream=None, chain_offset=0):
         self.lib = nat.load()
         els = [(int(m), int(n)) for m, n in elements]
         arr = (nat.ss_element * len(els))(*[nat.ss_element(m, n) for m, n in els])
@@ -36,6 +36,8 @@ class SlipSpring:
         nat.check(self.lib.ss_create(C.byref(h), arr, len(els), prec, int(seed), st), None, "ss_create")
         self.h = h
         self.params = None
+        if chain_offset:
+            self._chk(self.lib.ss_set_chain_offset(self.h, int(chain_offset)), "ss_set_chain_offset")
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -731,6 +731,19 @@ int ss_set_state(ss_ctx* c, int elem, const double* R, const int32_t* Z, const i
     return SS_OK;
 }
 
+int ss_set_chain_offset(ss_ctx* c, uint32_t offset) {
+    if (!c) return SS_EINVAL;
+    long long base = offset;
+    for (const Elem& e : c->el) base += e.M;
+    if (base > 0xFFFFFFFFll) return fail(c, SS_EINVAL, "chain ids would pass 2^32");
+    uint32_t b = offset;
+    for (Elem& e : c->el) {
+        e.chain_base = b;
+        b += (uint32_t)e.M;
+    }
+    return SS_OK;
+}
+
 int ss_step_count(ss_ctx* c, int64_t* steps) {
     if (!c || !steps) return SS_EINVAL;
     *steps = c->step;
