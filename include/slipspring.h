@@ -121,6 +121,25 @@ int ss_set_params(ss_ctx* ctx, const ss_params* p);
  * dynamic_equation_anchoring_position). */
 int ss_set_flow(ss_ctx* ctx, int elem, int64_t from_step, const double kappa[9]);
 
+/* Many entries of the flow schedule at once (the batched multiscale use, one
+ * velocity-gradient history per element): entry i sets kappa[9i..9i+8] for
+ * element elem[i] from step from_step[i] on, as ss_set_flow does; within an
+ * element the entries must be in increasing from_step order. */
+int ss_set_flow_table(ss_ctx* ctx, int n, const int32_t* elem, const int64_t* from_step, const double* kappa);
+
+/* Batched mode (support for many elements; not in the paper): when enabled,
+ * ss_run advances all elements with one persistent launch per chunk of
+ * chunk_steps steps, replayed from a captured CUDA graph; CTAs take (element,
+ * chain tile) work items from an atomic counter, longest chains first.  Before
+ * the first batched launch an autotuner times the candidate lane layouts of
+ * each chain length on a scratch ensemble and keeps the fastest (results
+ * cached per process).  Batched mode keeps the stress logs, not the
+ * correlator: ss_run fails with SS_EINVAL unless corr_levels < 0.  The
+ * numbers drawn and the results are those of the per-element path with the
+ * same layout.  enable = 0 returns to the per-element path and its default
+ * layouts. */
+int ss_set_batched(ss_ctx* ctx, int enable);
+
 /* Enqueue n_steps time steps for every element.  The first call on fresh state
  * samples the equilibrium initial state (Sec. 3.1: Gaussian chain, Poisson Z,
  * uniform S, Gaussian anchors).  Returns SS_EOVERFLOW if the step counter

@@ -67,6 +67,19 @@ class SlipSpring:
         k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(9))
         self._chk(self.lib.ss_set_flow(self.h, int(elem), int(from_step), _p(k, C.c_double)), "ss_set_flow")
 
+    def set_flow_table(self, elem, from_step, kappa):
+        """Many flow-schedule entries at once: element indices, first steps and
+        kappa matrices [n][3][3] (in increasing step order within an element)."""
+        e = np.ascontiguousarray(elem, dtype=np.int32)
+        f = np.ascontiguousarray(from_step, dtype=np.int64)
+        k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(len(e), 9))
+        self._chk(self.lib.ss_set_flow_table(self.h, len(e), _p(e, C.c_int32), _p(f, C.c_int64),
+                                             _p(k, C.c_double)), "ss_set_flow_table")
+
+    def set_batched(self, enable=True):
+        """One persistent, graph-replayed launch per chunk over all elements."""
+        self._chk(self.lib.ss_set_batched(self.h, 1 if enable else 0), "ss_set_batched")
+
     def run(self, n_steps):
         self._chk(self.lib.ss_run(self.h, int(n_steps)), "ss_run")
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,16 @@ struct Elem {
     bool flow_dirty = true;
 };
 
+// one layout class of the batched launch: its items, counter and graph node
+struct BatchedClass {
+    int k = 0;
+    int2* items = nullptr;
+    int n_items = 0;
+    unsigned* next = nullptr;
+    int grid = 1, smem = 0;
+    cudaGraphNode_t node = nullptr;
+};
+
 }  // namespace
 
 struct ss_ctx {
@@ -66,6 +77,16 @@ struct ss_ctx {
     long long launches = 0;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // chain-kernel launches while timing
+    // batched mode: one persistent launch per chunk over all elements
+    bool batched = false;
+    bool tuned = false;
+    bool graph_dirty = true;
+    ssk::ChunkArgs* d_elems = nullptr;
+    int2* d_items = nullptr;
+    unsigned* d_next = nullptr;
+    std::vector<BatchedClass> bclasses;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
     std::string err;
 };
 
@@ -314,6 +335,7 @@ int upload_flow(ss_ctx* c, Elem& e) {
     SS_CUDA(c, cudaStreamSynchronize(c->stream));
     e.n_kap_d = n;
     e.flow_dirty = false;
+    c->graph_dirty = true;
     return SS_OK;
 }
 
@@ -428,6 +450,354 @@ int chains_in_group(const Elem& e, int g) {
     return n;
 }
 
+// ------------------------------------------------------------ batched ----
+// Lane layouts the batched path can use; one persistent kernel per layout.
+constexpr int kBatchedLayouts = 5;
+constexpr int kLayoutW[kBatchedLayouts] = {16, 16, 16, 32, 8};
+constexpr int kLayoutB[kBatchedLayouts] = {1, 2, 3, 1, 2};
+
+int layout_class(int W, int B) {
+    for (int k = 0; k < kBatchedLayouts; ++k)
+        if (kLayoutW[k] == W && kLayoutB[k] == B) return k;
+    return -1;
+}
+
+void free_batched(ss_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->d_elems) cudaFree(c->d_elems);
+    if (c->d_items) cudaFree(c->d_items);
+    if (c->d_next) cudaFree(c->d_next);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->d_elems = nullptr;
+    c->d_items = nullptr;
+    c->d_next = nullptr;
+    c->bclasses.clear();
+    c->graph_dirty = true;
+}
+
+// one element's kernel arguments in batched mode (no correlator)
+ssk::ChunkArgs make_desc(const ss_ctx* c, const Elem& e) {
+    const ss_params& p = c->P;
+    ssk::ChunkArgs a{};
+    a.R = e.R;
+    a.A = e.A;
+    a.S = e.S;
+    a.Z = e.Z;
+    a.logs = e.logs;
+    a.counters = c->counters;
+    a.status = c->status;
+    a.kap = e.kap_d;
+    a.kap_from = e.kfrom_d;
+    a.n_kap = e.n_kap_d;
+    a.M = e.M;
+    a.N = e.N;
+    a.zmax = e.zmax;
+    a.create_mode = p.create_mode;
+    a.destroy_new = p.destroy_new;
+    a.levels = 0;
+    a.Lsm = 0;
+    a.log_every = p.log_every;
+    a.recenter_every = p.recenter_every;
+    a.max_logs = p.max_logs;
+    a.groups = e.groups;
+    a.slices = e.slices;
+    a.key0 = (uint32_t)c->seed;
+    a.key1 = (uint32_t)(c->seed >> 32);
+    a.chain_base = e.chain_base;
+    a.W = e.W;
+    a.B = e.B;
+    return a;
+}
+
+// Work items (element, first chain of a CTA tile) of one layout class,
+// longest chains and largest elements first.
+std::vector<int2> make_items(const std::vector<Elem>& el, int W, int B) {
+    std::vector<int> order;
+    for (size_t i = 0; i < el.size(); ++i)
+        if (el[i].W == W && el[i].B == B) order.push_back((int)i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return el[a].N != el[b].N ? el[a].N > el[b].N : el[a].M > el[b].M;
+    });
+    std::vector<int2> items;
+    for (int e : order) {
+        const int cpc = chains_per_cta(W);
+        for (int m = 0; m < el[e].M; m += cpc) items.push_back(make_int2(e, m));
+    }
+    return items;
+}
+
+template <typename T, int W, int B>
+const void* batched_fn() {
+    return (const void*)ssk::batched_kernel<T, W, B>;
+}
+
+template <typename T>
+const void* batched_fn_of(int k) {
+    switch (k) {
+        case 0: return batched_fn<T, 16, 1>();
+        case 1: return batched_fn<T, 16, 2>();
+        case 2: return batched_fn<T, 16, 3>();
+        case 3: return batched_fn<T, 32, 1>();
+        default: return batched_fn<T, 8, 2>();
+    }
+}
+
+template <typename T>
+int batched_smem_bytes(const ss_ctx* c, int k) {
+    const int nlog = c->P.log_every > 0 ? c->P.chunk_steps / c->P.log_every + 1 : 0;
+    return ssk::smem_plan<T>(kWarpsPerCta, kLayoutW[k], kLayoutB[k], 0, nlog).total;
+}
+
+// persistent grid size of class k: resident CTAs per SM x SMs, at most one per item
+template <typename T>
+int batched_grid(ss_ctx* c, int k, int n_items, int smem, int* grid) {
+    const void* fn = batched_fn_of<T>(k);
+    SS_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    SS_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+    SS_CUDA(c, cudaGetDevice(&dev));
+    SS_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    *grid = std::max(1, std::min(n_items, std::max(1, per_sm) * sms));
+    return SS_OK;
+}
+
+template <typename T>
+int batched_launch_direct(ss_ctx* c, int k, const ssk::ChunkArgs* d_elems, const int2* d_items, int n_items,
+                          unsigned* d_next, long long t0, int ns, int grid, int smem) {
+    SS_CUDA(c, cudaMemsetAsync(d_next, 0, sizeof(unsigned), c->stream));
+    ssk::RunInfo info{t0, ns, c->log_m0};
+    ssk::StepConst<T> sc = step_const<T>(c, 32);
+    void* args[] = {(void*)&d_elems, (void*)&d_items, (void*)&n_items, (void*)&d_next, (void*)&info, (void*)&sc};
+    SS_CUDA(c, cudaLaunchKernel(batched_fn_of<T>(k), dim3(grid), dim3(kThreads), args, smem, c->stream));
+    return SS_OK;
+}
+
+// Candidate lane layouts with the same padded stride NP as the default.
+std::vector<std::pair<int, int>> layout_candidates(int N) {
+    int W, B;
+    layout_for(N, &W, &B);
+    const int NP = W * B;
+    std::vector<std::pair<int, int>> cand = {{W, B}};
+    if (NP == 32) cand.push_back({32, 1});
+    if (NP == 16) cand.push_back({8, 2});
+    return cand;
+}
+
+// Project-written autotuner: for each chain length, time every candidate layout
+// on a trial ensemble (equilibrium start, no flow, no logs) with the batched
+// kernel of that layout and keep the fastest; results are cached per (N,
+// precision) for the process.
+template <typename T>
+int autotune(ss_ctx* c) {
+    static std::mutex mu;
+    static std::vector<std::array<int, 4>> cache;  // N, prec, W, B
+    std::vector<int> lengths;
+    for (const Elem& e : c->el)
+        if (std::find(lengths.begin(), lengths.end(), e.N) == lengths.end()) lengths.push_back(e.N);
+    for (int N : lengths) {
+        int bestW = -1, bestB = -1;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto& r : cache)
+                if (r[0] == N && r[1] == c->prec) bestW = r[2], bestB = r[3];
+        }
+        if (bestW < 0) {
+            auto cand = layout_candidates(N);
+            bestW = cand[0].first, bestB = cand[0].second;
+            if (cand.size() > 1) {
+                long long total = 0;
+                for (const Elem& e : c->el)
+                    if (e.N == N) total += e.M;
+                Elem t;
+                t.M = (int)std::max<long long>(256, std::min<long long>(8192, total));
+                t.N = N;
+                t.W = bestW;
+                t.B = bestB;
+                t.NP = t.W * t.B;
+                t.zmax = c->P.z_max > 0 ? std::min(c->P.z_max, N) : N;
+                t.slices = (t.M + ssk::kSliceChains - 1) / ssk::kSliceChains;
+                t.groups = 1;
+                const size_t ts = sizeof(T);
+                int rc = SS_OK;
+                if (cudaMalloc(&t.R, (size_t)t.M * 3 * t.NP * ts) != cudaSuccess ||
+                    cudaMalloc(&t.A, (size_t)t.M * 3 * t.NP * ts) != cudaSuccess ||
+                    cudaMalloc(&t.S, (size_t)t.M * t.NP * sizeof(int32_t)) != cudaSuccess ||
+                    cudaMalloc(&t.Z, (size_t)t.M * sizeof(int32_t)) != cudaSuccess)
+                    rc = fail(c, SS_ENOMEM, "autotune: allocation failed");
+                if (rc == SS_OK) rc = launch_init<T>(c, t);
+                if (rc == SS_OK) rc = upload_flow(c, t);
+                ssk::ChunkArgs* dd = nullptr;
+                int2* di = nullptr;
+                unsigned* dn = nullptr;
+                unsigned long long* dcnt = nullptr;  // the trials count into scratch, not the context
+                if (rc == SS_OK && (cudaMalloc(&dd, sizeof(ssk::ChunkArgs)) != cudaSuccess ||
+                                    cudaMalloc(&di, sizeof(int2) * ((t.M + 3) / 4 + 1)) != cudaSuccess ||
+                                    cudaMalloc(&dn, sizeof(unsigned)) != cudaSuccess ||
+                                    cudaMalloc(&dcnt, 16 * sizeof(unsigned long long)) != cudaSuccess))
+                    rc = fail(c, SS_ENOMEM, "autotune: allocation failed");
+                const long long saved_m0 = c->log_m0;
+                const int saved_log = c->P.log_every;
+                c->log_m0 = 0;
+                c->P.log_every = 0;
+                float best_ms = 1e30f;
+                for (auto& lb : cand) {
+                    if (rc != SS_OK) break;
+                    t.W = lb.first;
+                    t.B = lb.second;
+                    const int k = layout_class(t.W, t.B);
+                    std::vector<Elem> one = {t};
+                    std::vector<int2> items = make_items(one, t.W, t.B);
+                    ssk::ChunkArgs desc = make_desc(c, t);
+                    desc.counters = dcnt;
+                    desc.status = reinterpret_cast<int32_t*>(dcnt + 8);
+                    int grid = 1;
+                    const int smem = batched_smem_bytes<T>(c, k);
+                    rc = batched_grid<T>(c, k, (int)items.size(), smem, &grid);
+                    if (rc != SS_OK) break;
+                    SS_CUDA(c, cudaMemcpy(dd, &desc, sizeof(desc), cudaMemcpyHostToDevice));
+                    SS_CUDA(c, cudaMemcpy(di, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+                    cudaEvent_t e0, e1;
+                    SS_CUDA(c, cudaEventCreate(&e0));
+                    SS_CUDA(c, cudaEventCreate(&e1));
+                    rc = batched_launch_direct<T>(c, k, dd, di, (int)items.size(), dn, 0, 32, grid, smem);
+                    cudaEventRecord(e0, c->stream);
+                    if (rc == SS_OK)
+                        rc = batched_launch_direct<T>(c, k, dd, di, (int)items.size(), dn, 32, 256, grid, smem);
+                    cudaEventRecord(e1, c->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    if (rc == SS_OK && ms < best_ms) {
+                        best_ms = ms;
+                        bestW = lb.first;
+                        bestB = lb.second;
+                    }
+                }
+                c->log_m0 = saved_m0;
+                c->P.log_every = saved_log;
+                if (dd) cudaFree(dd);
+                if (di) cudaFree(di);
+                if (dn) cudaFree(dn);
+                if (dcnt) cudaFree(dcnt);
+                free_elem(t);
+                if (rc != SS_OK) return rc;
+                std::lock_guard<std::mutex> lk(mu);
+                cache.push_back({N, c->prec, bestW, bestB});
+            }
+        }
+        for (Elem& e : c->el)
+            if (e.N == N) e.W = bestW, e.B = bestB;
+    }
+    c->tuned = true;
+    c->graph_dirty = true;
+    return SS_OK;
+}
+
+// Descriptors, work items and the graph of one batched launch: per layout
+// class a counter reset and a persistent kernel, the classes on independent
+// branches so that they share the GPU.
+template <typename T>
+int batched_prepare(ss_ctx* c) {
+    free_batched(c);
+    std::vector<ssk::ChunkArgs> descs;
+    for (const Elem& e : c->el) descs.push_back(make_desc(c, e));
+    std::vector<std::vector<int2>> cls(kBatchedLayouts);
+    size_t total = 0;
+    for (int k = 0; k < kBatchedLayouts; ++k) {
+        cls[k] = make_items(c->el, kLayoutW[k], kLayoutB[k]);
+        total += cls[k].size();
+    }
+    SS_CUDA(c, cudaMalloc(&c->d_elems, sizeof(ssk::ChunkArgs) * descs.size()));
+    SS_CUDA(c, cudaMalloc(&c->d_items, sizeof(int2) * std::max<size_t>(1, total)));
+    SS_CUDA(c, cudaMalloc(&c->d_next, sizeof(unsigned) * kBatchedLayouts));
+    SS_CUDA(c, cudaMemcpy(c->d_elems, descs.data(), sizeof(ssk::ChunkArgs) * descs.size(), cudaMemcpyHostToDevice));
+    SS_CUDA(c, cudaGraphCreate(&c->graph, 0));
+    size_t off = 0;
+    for (int k = 0; k < kBatchedLayouts; ++k) {
+        if (cls[k].empty()) continue;
+        SS_CUDA(c, cudaMemcpy(c->d_items + off, cls[k].data(), sizeof(int2) * cls[k].size(), cudaMemcpyHostToDevice));
+        BatchedClass bc;
+        bc.k = k;
+        bc.items = c->d_items + off;
+        bc.n_items = (int)cls[k].size();
+        bc.next = c->d_next + k;
+        bc.smem = batched_smem_bytes<T>(c, k);
+        int rc = batched_grid<T>(c, k, bc.n_items, bc.smem, &bc.grid);
+        if (rc != SS_OK) return rc;
+        cudaMemsetParams mp{};
+        mp.dst = bc.next;
+        mp.value = 0;
+        mp.elementSize = sizeof(unsigned);
+        mp.width = 1;
+        mp.height = 1;
+        cudaGraphNode_t mnode;
+        SS_CUDA(c, cudaGraphAddMemsetNode(&mnode, c->graph, nullptr, 0, &mp));
+        ssk::RunInfo info{0, 1, 0};
+        ssk::StepConst<T> sc = step_const<T>(c, 32);
+        const ssk::ChunkArgs* pe = c->d_elems;
+        void* args[] = {(void*)&pe, (void*)&bc.items, (void*)&bc.n_items, (void*)&bc.next, (void*)&info, (void*)&sc};
+        cudaKernelNodeParams kp{};
+        kp.func = (void*)batched_fn_of<T>(k);
+        kp.gridDim = dim3(bc.grid);
+        kp.blockDim = dim3(kThreads);
+        kp.sharedMemBytes = bc.smem;
+        kp.kernelParams = args;
+        SS_CUDA(c, cudaGraphAddKernelNode(&bc.node, c->graph, &mnode, 1, &kp));
+        c->bclasses.push_back(bc);
+        off += cls[k].size();
+    }
+    SS_CUDA(c, cudaGraphInstantiate(&c->gexec, c->graph, 0));
+    c->graph_dirty = false;
+    return SS_OK;
+}
+
+// One graph launch per chunk; the chunk's first step enters through the kernel
+// nodes' parameters.
+template <typename T>
+int batched_chunk(ss_ctx* c, long long t0, int ns) {
+    ssk::RunInfo info{t0, ns, c->log_m0};
+    ssk::StepConst<T> sc = step_const<T>(c, 32);
+    const ssk::ChunkArgs* pe = c->d_elems;
+    for (BatchedClass& bc : c->bclasses) {
+        void* args[] = {(void*)&pe, (void*)&bc.items, (void*)&bc.n_items, (void*)&bc.next, (void*)&info, (void*)&sc};
+        cudaKernelNodeParams kp{};
+        kp.func = (void*)batched_fn_of<T>(bc.k);
+        kp.gridDim = dim3(bc.grid);
+        kp.blockDim = dim3(kThreads);
+        kp.sharedMemBytes = bc.smem;
+        kp.kernelParams = args;
+        SS_CUDA(c, cudaGraphExecKernelNodeSetParams(c->gexec, bc.node, &kp));
+    }
+    SS_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+    c->launches += (long long)c->bclasses.size();
+    return SS_OK;
+}
+
+template <typename T>
+int batched_run(ss_ctx* c, long long n_steps) {
+    if (!c->tuned) {
+        int rc = autotune<T>(c);
+        if (rc != SS_OK) return rc;
+    }
+    if (c->graph_dirty) {
+        int rc = batched_prepare<T>(c);
+        if (rc != SS_OK) return rc;
+    }
+    long long left = n_steps;
+    while (left > 0) {
+        const int ns = (int)std::min<long long>(left, c->P.chunk_steps);
+        int rc = batched_chunk<T>(c, c->step, ns);
+        if (rc != SS_OK) return rc;
+        c->step += ns;
+        left -= ns;
+    }
+    return SS_OK;
+}
+
 }  // namespace
 
 // ================================================================== C ABI ====
@@ -507,6 +877,7 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
     }
     if (c->counters) cudaStreamSynchronize(c->stream);
     for (Elem& e : c->el) free_elem(e);
+    free_batched(c);
     c->P = p;
     c->k_b = kb;
     c->k_s = ks;
@@ -561,6 +932,32 @@ int ss_set_flow(ss_ctx* c, int elem, int64_t from_step, const double kappa[9]) {
         for (int k = 0; k < 9; ++k) e.kap[9 * n + k] = kappa[k];
         e.flow_dirty = true;
     }
+    c->graph_dirty = true;
+    return SS_OK;
+}
+
+int ss_set_flow_table(ss_ctx* c, int n, const int32_t* elem, const int64_t* from_step, const double* kappa) {
+    if (!c || n < 0 || (n > 0 && (!elem || !from_step || !kappa))) return SS_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (elem[i] < 0 || elem[i] >= (int)c->el.size()) return fail(c, SS_EINVAL, "bad element index");
+        if (i > 0 && elem[i] == elem[i - 1] && from_step[i] <= from_step[i - 1])
+            return fail(c, SS_EINVAL, "flow table: steps must increase within an element");
+    }
+    for (int i = 0; i < n; ++i) {
+        const int rc = ss_set_flow(c, elem[i], from_step[i], kappa + 9 * (size_t)i);
+        if (rc != SS_OK) return rc;
+    }
+    return SS_OK;
+}
+
+int ss_set_batched(ss_ctx* c, int enable) {
+    if (!c) return SS_EINVAL;
+    c->batched = enable != 0;
+    c->graph_dirty = true;
+    if (!c->batched) {  // back to the per-element kernels' layouts (same padded stride)
+        for (Elem& e : c->el) layout_for(e.N, &e.W, &e.B);
+        c->tuned = false;
+    }
     return SS_OK;
 }
 
@@ -584,6 +981,10 @@ int ss_run(ss_ctx* c, int64_t n_steps) {
             if (rc != SS_OK) return rc;
         }
         c->initialized = true;
+    }
+    if (c->batched) {
+        if (c->levels > 0) return fail(c, SS_EINVAL, "batched mode keeps stress logs only: set corr_levels < 0");
+        return c->prec == SS_FP64 ? batched_run<double>(c, n_steps) : batched_run<float>(c, n_steps);
     }
     long long left = n_steps;
     while (left > 0) {
@@ -684,6 +1085,7 @@ int ss_destroy(ss_ctx* c) {
         cudaEventDestroy(pr.second);
     }
     for (Elem& e : c->el) free_elem(e);
+    free_batched(c);
     if (c->counters) cudaFree(c->counters);
     if (c->status) cudaFree(c->status);
     delete c;

@@ -166,6 +166,7 @@ struct ChunkArgs {
     long long nsamp0;           // correlator samples per chain before this launch
     uint32_t key0, key1, chain_base;
     int nlog_chunk;             // log slots reserved in shared memory
+    int W, B;                   // lane layout (read by the batched kernel)
 };
 
 // One slip-spring slot as the force loop reads it from shared memory:
@@ -325,9 +326,12 @@ __device__ __forceinline__ void corr_level_from_below(const T (&hprev)[3][CPL], 
 // ---------------------------------------------------------- chunk kernel ----
 // W lanes per chain, B beads per lane: bead i and slot i of a chain live on
 // lane i % W as its sub-slot i / W (NP = W*B >= N beads and slots).
+// The chains of one CTA: chains cta_first .. cta_first + chains per CTA - 1 of
+// the element described by `a` (all warps of the CTA call this together).
 template <typename T, int W, int B>
-__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_MULTI)
-    chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
+__device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T>& c, const int cta_first,
+                                           const T NkT, const long long t0_, const int nsteps_,
+                                           const long long log_m0_, const int nlog_) {
     constexpr int SEGS = 32 / W;
     constexpr int NP = W * B;
     constexpr int CPL = kCells / W;  // correlator cells per lane
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
     const int ll = lane % W;
     const int cpc = nwarps * SEGS;  // chains per CTA
     const int cslot = warp * SEGS + seg;
-    const int m = blockIdx.x * cpc + cslot;
+    const int m = cta_first + cslot;
     const bool live = m < a.M;
     const int mm = live ? m : 0;
     const uint32_t chain_id = a.chain_base + (uint32_t)mm;
@@ -350,14 +354,14 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
     const unsigned lt = ((1u << lane) - 1u) & segmask;  // lanes of this segment below this one
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemPlan plan = smem_plan<T>(nwarps, W, B, a.Lsm, a.nlog_chunk);
+    const SmemPlan plan = smem_plan<T>(nwarps, W, B, a.Lsm, nlog_);
     SlotRec<T>* tab = reinterpret_cast<SlotRec<T>*>(smem + plan.off_tab) + (warp * SEGS + seg) * NP;
     Pos<T>* pos = reinterpret_cast<Pos<T>*>(smem + plan.off_pos) + (warp * SEGS + seg) * NP;
     Mask* msk = reinterpret_cast<Mask*>(smem + plan.off_msk) + (warp * SEGS + seg) * NP;
     double* slog = reinterpret_cast<double*>(smem + plan.off_log);
     T* scorr = reinterpret_cast<T*>(smem + plan.off_corr);
 
-    for (int i = threadIdx.x; i < a.nlog_chunk * 14; i += blockDim.x) slog[i] = 0.0;
+    for (int i = threadIdx.x; i < nlog_ * 14; i += blockDim.x) slog[i] = 0.0;
 
     // ---- load state
     const T* Rg = static_cast<const T*>(a.R);
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
                 }
         }
     }
-    if (a.nlog_chunk > 0)
+    if (nlog_ > 0)
         __syncthreads();  // the CTA's stress-log buffer is zeroed
     else
         __syncwarp();
@@ -422,11 +426,11 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
     // ---- flow schedule and periodic events, as step offsets in this launch
     const int never = 0x7fffffff;
     auto rel = [&](long long t_abs) -> int {
-        const long long r = t_abs - a.t0;
+        const long long r = t_abs - t0_;
         return r > (long long)never ? never : (int)r;
     };
     int ki = 0;
-    while (ki + 1 < a.n_kap && a.t0 >= a.kap_from[ki + 1]) ++ki;
+    while (ki + 1 < a.n_kap && t0_ >= a.kap_from[ki + 1]) ++ki;
     T kap[9];
     bool kap_nz = false;
 #pragma unroll
@@ -435,18 +439,18 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
         kap_nz |= (kap[i] != T(0));
     }
     int next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
-    int next_log = a.log_every > 0 ? rel((a.t0 / a.log_every + 1) * a.log_every - 1) : never;
-    int next_rc = a.recenter_every > 0 ? rel((a.t0 / a.recenter_every + 1) * a.recenter_every - 1) : never;
+    int next_log = a.log_every > 0 ? rel((t0_ / a.log_every + 1) * a.log_every - 1) : never;
+    int next_rc = a.recenter_every > 0 ? rel((t0_ / a.recenter_every + 1) * a.recenter_every - 1) : never;
     int log_slot = 0;
-    const uint32_t t0lo = (uint32_t)a.t0;
+    const uint32_t t0lo = (uint32_t)t0_;
     const uint32_t n0lo = (uint32_t)a.nsamp0;
 
     unsigned cnt_up = 0, cnt_dn = 0, cnt_cr = 0, cnt_de = 0, cnt_drop = 0;
 
-    for (int s = 0; s < a.nsteps; ++s) {
+    for (int s = 0; s < nsteps_; ++s) {
         const uint32_t t = t0lo + (uint32_t)s;
         if (s >= next_from) {
-            while (ki + 1 < a.n_kap && a.t0 + s >= a.kap_from[ki + 1]) ++ki;
+            while (ki + 1 < a.n_kap && t0_ + s >= a.kap_from[ki + 1]) ++ki;
             kap_nz = false;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -754,9 +758,9 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
             if (do_log) {
                 T dg[3];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) dg[d] = seg_sum<T, W>(dgp[d]) - c.NkT;
+                for (int d = 0; d < 3; ++d) dg[d] = seg_sum<T, W>(dgp[d]) - NkT;
                 const int slot = log_slot++;
-                if (live && ll == 0 && slot < a.nlog_chunk) {
+                if (live && ll == 0 && slot < nlog_) {
                     double* L = slog + slot * 14;
                     const double v6[6] = {(double)dg[0], (double)dg[1], (double)dg[2],
                                           (double)sig[0], (double)sig[1], (double)sig[2]};
@@ -887,9 +891,10 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
         atomicAdd(a.counters + 6, 1ull);
     }
 
-    // ---- event counters
+    // ---- event counters (padding segments beyond the element's chains count nothing)
     {
         unsigned v[5] = {cnt_up, cnt_dn, cnt_cr, cnt_de, cnt_drop};
+        if (!live) v[0] = v[1] = v[2] = v[3] = v[4] = 0u;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             unsigned x = v[k];
@@ -927,18 +932,55 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
     }
 
     // ---- stress logs: add this CTA's sums to its group
-    if (a.log_every > 0 && a.nlog_chunk > 0) {
+    if (a.log_every > 0 && nlog_ > 0) {
         __syncthreads();
-        const long long first_m = a.t0 / a.log_every + 1;  // first log multiple in or after t0+1
-        const int slice = (int)(((long long)blockIdx.x * cpc) / kSliceChains);
+        const long long first_m = t0_ / a.log_every + 1;  // first log multiple in or after t0+1
+        const int slice = cta_first / kSliceChains;
         const int grp = (int)(((long long)slice * a.groups) / a.slices);
-        for (int i = threadIdx.x; i < a.nlog_chunk * 14; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nlog_ * 14; i += blockDim.x) {
             const int slot = i / 14, k = i % 14;
-            const long long idx = first_m + slot - a.log_m0 - 1;
+            const long long idx = first_m + slot - log_m0_ - 1;
             const long long step = (first_m + slot) * a.log_every;
-            if (step <= a.t0 + a.nsteps && idx >= 0 && idx < a.max_logs && slog[i] != 0.0)
+            if (step <= t0_ + nsteps_ && idx >= 0 && idx < a.max_logs && slog[i] != 0.0)
                 atomicAdd(a.logs + ((size_t)idx * a.groups + grp) * 14 + k, slog[i]);
         }
+    }
+}
+
+template <typename T, int W, int B>
+__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_MULTI)
+    chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
+    run_chains<T, W, B>(a, c, blockIdx.x * (kChunkThreads / W), c.NkT, a.t0, a.nsteps, a.log_m0, a.nlog_chunk);
+}
+
+// ------------------------------------------------------ batched kernel ------
+// Many elements in one persistent launch per lane layout: each CTA takes work
+// items (element, first chain of a CTA tile) of its layout class from an
+// atomic counter until the list is exhausted, and runs the tile for all steps
+// of the launch.  The counter is only ever incremented: no CTA waits for
+// another.  Each element's arguments (state pointers, sizes, flow schedule,
+// log buffers) live in a device array and are read in place.
+struct RunInfo {
+    long long t0;     // first step of this launch
+    int nsteps;
+    long long log_m0;
+};
+
+template <typename T, int W, int B>
+__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_MULTI)
+    batched_kernel(const ChunkArgs* __restrict__ elems, const int2* __restrict__ items, int n_items,
+                   unsigned* __restrict__ next_item, const RunInfo info, const StepConst<T> c) {
+    __shared__ int item_s;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item_s = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int it = item_s;
+        if (it >= n_items) break;
+        const int2 wi = items[it];
+        const ChunkArgs& a = elems[wi.x];
+        const int nlog = a.log_every > 0 ? (int)((info.t0 + info.nsteps) / a.log_every - info.t0 / a.log_every) : 0;
+        run_chains<T, W, B>(a, c, wi.y, T((double)a.N) * c.kT, info.t0, info.nsteps, info.log_m0, nlog);
     }
 }
 

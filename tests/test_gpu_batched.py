@@ -1,0 +1,160 @@
+"""Batched multiscale path: many elements (own ensemble size, chain length and
+velocity-gradient history) advanced by one graph launch of persistent kernels.
+
+* The batched path draws the same numbers as the per-element path, so the
+  states are identical and the stress logs agree to rounding of the
+  differently ordered FP32/FP64 reductions.
+* FP64 parity with the oracle on sampled chains of several elements, each
+  with its own traceless flow history.
+* The full-size multiscale workload (4096 elements, sizes log-uniform in
+  64..1024, lengths in {16, 24, 32, 48}, Gaussian traceless kappa with std 1e-2
+  redrawn every 1000 steps): invariants for every chain, sampled chains against
+  the oracle until a near-tie, and the throughput printed for the record.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import Params
+from paper_1106_2899_gb300 import SlipSpring
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu(cuda_ok):
+    from paper_1106_2899_gb300 import build
+    build.build()
+    yield
+
+
+def _flow_table(Ms, n_draws, every, seed):
+    rng = np.random.default_rng(seed)
+    elem, frm, kap = [], [], []
+    for e in range(len(Ms)):
+        for d in range(n_draws):
+            k = rng.normal(0, 0.05, size=(3, 3))
+            k -= np.trace(k) / 3 * np.eye(3)
+            elem.append(e)
+            frm.append(d * every)
+            kap.append(k)
+    return np.array(elem), np.array(frm), np.array(kap)
+
+
+def _ctx(els, precision, log_every, max_logs, batched):
+    g = SlipSpring(els, precision=precision, seed=13)
+    g.set_params(**synth.PAPER, corr_levels=-1, groups=4, log_every=log_every, max_logs=max_logs, chunk_steps=200)
+    if batched:
+        g.set_batched(True)
+    return g
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batched_equals_per_element_path(precision):
+    els = [(100, 16), (77, 24), (130, 32), (65, 48), (9, 20), (200, 32)]
+    elem, frm, kap = _flow_table([m for m, _ in els], 3, 150, seed=1)
+    steps, log_every = 500, 50
+    out = {}
+    for batched in (False, True):
+        g = _ctx(els, precision, log_every, steps // log_every, batched)
+        g.set_flow_table(elem, frm, kap)
+        g.run(steps)
+        out[batched] = ([g.get_state(e) for e in range(len(els))], [g.log_sums(e) for e in range(len(els))],
+                        g.counters())
+        assert g.status() == 0
+    for e in range(len(els)):
+        a, b = out[False][0][e], out[True][0][e]
+        assert np.array_equal(a["Z"], b["Z"]) and np.array_equal(a["S"], b["S"]), e
+        assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["A"], b["A"]), e
+        (ta, La), (tb, Lb) = out[False][1][e], out[True][1][e]
+        assert np.array_equal(ta, tb)
+        tol = 1e-5 if precision == "fp32" else 1e-12
+        assert np.allclose(La, Lb, rtol=tol, atol=tol * np.abs(La).max())
+    for k in ("hops_up", "hops_down", "created", "destroyed"):
+        assert out[False][2][k] == out[True][2][k]
+
+
+def test_batched_fp64_matches_oracle_on_sampled_chains():
+    els = [(40, 16), (33, 24), (50, 32), (21, 48)]
+    elem, frm, kap = _flow_table([m for m, _ in els], 4, 100, seed=2)
+    steps = 400
+    g = _ctx(els, "fp64", 0, 0, True)
+    g.set_flow_table(elem, frm, kap)
+    g.run(steps)
+    base = 0
+    rng = np.random.default_rng(3)
+    for e, (M, N) in enumerate(els):
+        st = g.get_state(e)
+        for m in rng.choice(M, size=4, replace=False):
+            p = Params(N=N, **synth.PAPER)
+            o = oracle.Ensemble(p, seed=13, M=1, chain_offset=base + int(m), levels=1)
+            for i in np.nonzero(elem == e)[0]:
+                o.set_flow(int(frm[i]), kap[i])
+            o.init()
+            o.run(steps)
+            oo = o.get_state()
+            assert oo["Z"][0] == st["Z"][m] and np.array_equal(oo["S"][0], st["S"][m]), (e, m)
+            c = oo["R"][0].mean(axis=0)
+            cg = st["R"][m].mean(axis=0)
+            assert np.allclose(oo["R"][0] - c, st["R"][m] - cg, atol=1e-10)
+        base += M
+
+
+@pytest.mark.slow
+def test_multiscale_workload_full_size():
+    w = synth.WORKLOADS["batched"]
+    Ms, Ns, G = synth.element_table(w["n_elements"], seed=w["seed"], lengths=w["lengths"], m_lo=w["m_lo"],
+                                    m_hi=w["m_hi"], n_kappa=3, kappa_std=w["kappa_std"])
+    els = [(int(m), int(n)) for m, n in zip(Ms, Ns)]
+    steps, every, log_every = 2000, w["kappa_every"], 100
+    g = SlipSpring(els, precision="fp32", seed=w["seed"])
+    g.set_params(**synth.PAPER, corr_levels=-1, groups=4, log_every=log_every, max_logs=steps // log_every,
+                 chunk_steps=1000)
+    g.set_batched(True)
+    elem = np.repeat(np.arange(len(els)), 2)
+    frm = np.tile([0, every], len(els))
+    kap = G[:, :2].reshape(-1, 3, 3)
+    g.set_flow_table(elem, frm, kap)
+    g.run(0)
+    c0 = g.counters()
+    z0 = sum(int(g.get_state(e)["Z"].sum()) for e in range(0, len(els), 1))
+    g.run(1000)  # autotune + first graph launch
+    g.synchronize()
+    t = time.perf_counter()
+    g.run(steps - 1000)
+    g.synchronize()
+    dt = time.perf_counter() - t
+    beads = float(sum(m * n for m, n in els))
+    print("\nmultiscale workload: %d elements, %d chains, %.3g beads: %.3g bead-steps/s"
+          % (len(els), sum(m for m, _ in els), beads, beads * (steps - 1000) / dt))
+    assert g.status() == 0
+    c = g.counters()
+    zs = 0
+    base = 0
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(len(els), size=12, replace=False).tolist())
+    agree = 0
+    for e, (M, N) in enumerate(els):
+        st = g.get_state(e)
+        assert np.all((st["Z"] >= 0) & (st["Z"] <= N)) and np.all(np.isfinite(st["R"]))
+        zs += int(st["Z"].sum())
+        if e in sample:
+            m = int(rng.integers(M))
+            p = Params(N=N, **synth.PAPER)
+            o = oracle.Ensemble(p, seed=w["seed"], M=1, chain_offset=base + m, levels=1)
+            o.set_flow(0, kap[2 * e])
+            o.set_flow(every, kap[2 * e + 1])
+            o.init()
+            _, _, mg = o.run(steps, trace=True)
+            if not np.any(mg[:, 0] < 1e-5):
+                oo = o.get_state()
+                assert oo["Z"][0] == st["Z"][m] and np.array_equal(oo["S"][0], st["S"][m]), (e, m)
+                agree += 1
+        base += M
+    assert zs - z0 == (c["created"] - c0["created"]) - (c["destroyed"] - c0["destroyed"])
+    assert agree >= 1
+    t_log, L = g.log_sums(0)
+    assert len(t_log) == steps // log_every

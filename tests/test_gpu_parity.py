@@ -103,6 +103,10 @@ def _fp64_stepwise(p, M, seed, steps_each, blocks, kappa=None, start=None, level
         g.run(steps_each)
         o.run(steps_each)
         _compare_states(g.get_state(), o.get_state(), np.ones(M, bool), 1e-10, "block %d" % b)
+    # event counters are integers: equal, whatever the padding of the last CTA
+    gc, oc = g.counters(), o.counters()
+    for k in ("hops_up", "hops_down", "created", "destroyed", "dropped"):
+        assert gc[k] == oc[k], k
     return g, o
 
 
