@@ -188,6 +188,11 @@ int ss_set_chain_offset(ss_ctx* ctx, uint32_t offset);
 
 /* Steps taken so far. */
 int ss_step_count(ss_ctx* ctx, int64_t* steps);
+/* Set the step counter (resume from a saved state: the next step draws the
+ * Philox numbers of step `step`, Sec. 3.1 with the counter mapping above).
+ * The observables are reset, as by ss_reset_observables, so that correlator
+ * and log windows start at the new step.  SS_EINVAL outside 0..2^32. */
+int ss_set_step_count(ss_ctx* ctx, int64_t step);
 
 /* Zero the correlator and the stress logs (e.g. after equilibration). */
 int ss_reset_observables(ss_ctx* ctx);
@@ -225,6 +230,40 @@ int ss_synchronize(ss_ctx* ctx);
  * enable = 0 stops recording. */
 int ss_kernel_timing(ss_ctx* ctx, int enable);
 int ss_kernel_time(ss_ctx* ctx, double* chain_kernel_ms, int64_t* chain_launches);
+
+/* ---- differentiation windows (pathwise gradients; not in the paper) --------
+ * A window of n_steps steps from the current state of a one-element context
+ * with the correlator enabled and no flow.  The loss is a function L(G) of the
+ * TOTAL channel of the relaxation modulus G measured over the window alone
+ * (Eq. relaxation_modulus_tensor_green_kubo_form, App. B); the gradient is
+ * the pathwise derivative of L with respect to (k_b, k_s, zeta) with every
+ * discrete decision (hop, creation, destruction) frozen along the trajectory.
+ *
+ * ss_window_forward runs the window, resetting the observables at its start,
+ * saving the state every checkpoint_every steps (checkpoint_every <=
+ * chunk_steps; the last segment may be shorter) and the stress series of every
+ * step.
+ * replay = 0 records the decisions on a tape; replay = 1 re-runs a window of
+ * the same length from the current state with the recorded decisions and the
+ * recorded window's step indices, hence the same Gaussian noise (for finite
+ * differences of the frozen-decision map at other parameters set with
+ * ss_set_coefficients); the continuous update uses the current parameters
+ * either way.  Device memory grows with n_steps x chains.
+ *
+ * ss_window_backward takes dL/dG for each multiple-tau slot of the TOTAL
+ * channel, dL_dG[level][16] (G as returned by ss_correlator; unused slots 0),
+ * and writes grad = dL/d(k_b, k_s, zeta).  It runs a hand-written adjoint of
+ * the continuous update backwards through the window, recomputing each
+ * checkpoint segment forward (with the recorded decisions) to obtain the
+ * states it needs.  The live state is the window's final state afterwards. */
+int ss_window_forward(ss_ctx* ctx, int64_t n_steps, int checkpoint_every, int replay);
+/* Set the bond stiffness k_b, the slip-spring stiffness k_s and the bead
+ * friction zeta (Sec. 3.1) without touching the state, the step counter, the
+ * observables or a recorded window (ss_set_params would reset all of them).
+ * SS_EINVAL for a non-positive value or an unstable Euler step
+ * (dt (4 k_b + k_s) / zeta >= 2); SS_ESTATE before ss_set_params. */
+int ss_set_coefficients(ss_ctx* ctx, double k_b, double k_s, double zeta);
+int ss_window_backward(ss_ctx* ctx, const double* dL_dG, double grad[3]);
 
 /* ---- allocation-free run ---------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot

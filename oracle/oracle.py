@@ -71,6 +71,10 @@ def _load():
     lib.or_ens_reset_obs.argtypes = [C.c_void_p]
     lib.or_ens_counters.argtypes = [C.c_void_p, lp]
     lib.or_corr_series.argtypes = [dp, C.c_int64, C.c_int, dp]
+    lib.or_ens_run_tape.argtypes = [C.c_void_p, C.c_int64, C.c_int, ip, ip, dp, P(C.c_uint8), C.c_int]
+    lib.or_ens_run_tape.restype = C.c_int
+    lib.or_ens_set_step.argtypes = [C.c_void_p, C.c_int64]
+    lib.or_ens_set_step.restype = None
     _lib = lib
     return lib
 
@@ -241,9 +245,22 @@ class Ensemble:
             raise RuntimeError("oracle: log capacity exceeded")
         return (Z, S, mg) if trace else None
 
+    def run_tape(self, n_steps, tape, mode, nthreads=0):
+        """Advance n_steps recording (mode 1) or replaying (mode 2) the decision
+        tape, a uint8 array [n_steps][M][N]."""
+        assert tape.dtype == np.uint8 and tape.shape == (n_steps, self.M, self.N) and tape.flags.c_contiguous
+        rc = self.lib.or_ens_run_tape(self.h, int(n_steps), int(nthreads), None, None, None,
+                                      _ptr(tape, C.c_uint8), int(mode))
+        if rc != 0:
+            raise RuntimeError("oracle: log capacity exceeded")
+
     @property
     def step(self):
         return self.lib.or_ens_step(self.h)
+
+    @step.setter
+    def step(self, value):
+        self.lib.or_ens_set_step(self.h, int(value))
 
     def get_state(self):
         R = np.zeros((self.M, self.N, 3))

@@ -165,6 +165,9 @@ void or_init_chain(const or_params* p, const uint32_t key[2], uint32_t chain_id,
 }
 
 /* ------------------------------------------------------------------ step -- */
+void or_step_chain_tape(const or_params* p, const uint32_t key[2], uint32_t chain_id, uint32_t step,
+                        const double kap[9], double cd, or_chain* c, or_step_info* info, const uint8_t* replay,
+                        uint8_t* record);
 static double or_dist2(const double x[3], const double y[3]) {
     double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
     return d0 * d0 + d1 * d1 + d2 * d2;
@@ -190,6 +193,19 @@ static void or_margin(double* m, double a, double b) {
 
 void or_step_chain(const or_params* p, const uint32_t key[2], uint32_t chain_id, uint32_t step,
                    const double kap[9], double cd, or_chain* c, or_step_info* info) {
+    or_step_chain_tape(p, key, chain_id, step, kap, cd, c, info, NULL, NULL);
+}
+
+/* Decision tape (test support for frozen-decision finite differences): one
+ * byte per slot/attempt index j and step; bit 0: spring j hopped to S+1, bit 1:
+ * to S-1, bit 2: attempt j created a spring at bead 1, bit 3: at bead N, bit 4:
+ * old spring j destroyed, bit 5: the spring created by attempt j destroyed.
+ * With `replay` the decisions are read instead of drawn. */
+void or_step_chain_tape(const or_params* p, const uint32_t key[2], uint32_t chain_id, uint32_t step,
+                        const double kap[9], double cd, or_chain* c, or_step_info* info, const uint8_t* replay,
+                        uint8_t* record) {
+    uint8_t tape[OR_NMAX];
+    memset(tape, 0, sizeof(tape));
     const int N = p->N;
     double nrm[OR_NMAX][4], uni[OR_NMAX];
     for (int i = 0; i < N; ++i) {
@@ -242,12 +258,19 @@ void or_step_chain(const or_params* p, const uint32_t key[2], uint32_t chain_id,
         double u = uni[j];
         or_margin(&inf.min_margin, u, pp);
         or_margin(&inf.min_margin, u, pp + pm);
-        if (u < pp) {
+        int up = u < pp, down = !up && u < pp + pm;
+        if (replay) {
+            up = (replay[j] & 1) != 0;
+            down = (replay[j] & 2) != 0;
+        }
+        if (up) {
             c->S[j] = s + 1;
             inf.hops_up++;
-        } else if (u < pp + pm) {
+            tape[j] |= 1;
+        } else if (down) {
             c->S[j] = s - 1;
             inf.hops_down++;
+            tape[j] |= 2;
         }
     }
 
@@ -274,7 +297,9 @@ void or_step_chain(const or_params* p, const uint32_t key[2], uint32_t chain_id,
                 end = 0;
             else if (u < 2.0 * pc)
                 end = N - 1;
+            if (replay) end = (replay[j] & 4) ? 0 : ((replay[j] & 8) ? N - 1 : -1);
             if (end < 0) continue;
+            tape[j] |= end == 0 ? 4 : 8;
             uint32_t w[4];
             double n[4], uu;
             or_block(key, (uint32_t)j, step, OR_PURPOSE_CREATE, chain_id, w);
@@ -294,18 +319,24 @@ void or_step_chain(const or_params* p, const uint32_t key[2], uint32_t chain_id,
         int s = c->S[j];
         if (s == 0 || s == N - 1) {
             or_margin(&inf.min_margin, nrm[j][3], cd);
-            if (nrm[j][3] < cd) {
+            int kill = nrm[j][3] < cd;
+            if (replay) kill = (replay[j] & 16) != 0;
+            if (kill) {
                 alive[j] = 0;
                 inf.destroyed++;
+                tape[j] |= 16;
             }
         }
     }
     for (int j = first; j < last; ++j) {
         if (new_end[j] < 0 || !p->destroy_new) continue;
         or_margin(&inf.min_margin, nrm[j][3], cd);
-        if (nrm[j][3] < cd) {
+        int kill = nrm[j][3] < cd;
+        if (replay) kill = (replay[j] & 32) != 0;
+        if (kill) {
             new_end[j] = -2; /* created and destroyed within the step */
             inf.destroyed++;
+            tape[j] |= 32;
         }
     }
 
@@ -334,6 +365,7 @@ void or_step_chain(const or_params* p, const uint32_t key[2], uint32_t chain_id,
         memcpy(c->A[j], out.A[j], sizeof(double) * 3);
     }
     for (int j = z; j < OR_NMAX; ++j) c->S[j] = 0;
+    if (record) memcpy(record, tape, (size_t)N);
     if (info) *info = inf;
 }
 
@@ -494,6 +526,11 @@ static const double* or_kappa_at(const or_ens* e, int64_t t) {
 
 int or_ens_run(or_ens* e, int64_t n_steps, int nthreads, int32_t* Z_tr, int32_t* S_tr,
                double* margin_tr) {
+    return or_ens_run_tape(e, n_steps, nthreads, Z_tr, S_tr, margin_tr, NULL, 0);
+}
+
+int or_ens_run_tape(or_ens* e, int64_t n_steps, int nthreads, int32_t* Z_tr, int32_t* S_tr,
+                    double* margin_tr, uint8_t* tape, int tape_mode) {
     const int M = e->M, G = e->G, zmax = e->p.z_max;
     const int64_t t0 = e->step;
     const size_t per_acc = (size_t)e->levels * OR_P * 6;
@@ -521,8 +558,9 @@ int or_ens_run(or_ens* e, int64_t n_steps, int nthreads, int32_t* Z_tr, int32_t*
             for (int64_t s = 0; s < n_steps; ++s) {
                 int64_t t = t0 + s;
                 or_step_info info;
-                or_step_chain(&e->p, e->key, e->chain_offset + (uint32_t)m, (uint32_t)t,
-                              or_kappa_at(e, t), e->cd, c, &info);
+                uint8_t* row = tape ? tape + ((size_t)s * M + m) * (size_t)e->p.N : NULL;
+                or_step_chain_tape(&e->p, e->key, e->chain_offset + (uint32_t)m, (uint32_t)t, or_kappa_at(e, t),
+                                   e->cd, c, &info, tape_mode == 2 ? row : NULL, tape_mode == 1 ? row : NULL);
                 cnt[0] += info.hops_up;
                 cnt[1] += info.hops_down;
                 cnt[2] += info.created;
@@ -587,6 +625,8 @@ void or_ens_set_state(or_ens* e, const double* R, const int32_t* Z, const int32_
 }
 
 int64_t or_ens_step(const or_ens* e) { return e->step; }
+
+void or_ens_set_step(or_ens* e, int64_t step) { e->step = step; }
 
 void or_ens_corr(const or_ens* e, double* acc, int64_t* n_samples) {
     memcpy(acc, e->acc, sizeof(double) * (size_t)e->G * e->levels * OR_P * 6);

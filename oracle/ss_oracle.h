@@ -100,6 +100,16 @@ typedef struct {
 void or_step_chain(const or_params* p, const uint32_t key[2], uint32_t chain_id, uint32_t step,
                    const double kappa[9], double cd, or_chain* c, or_step_info* info);
 
+/* The same step with a decision tape (test support for frozen-decision
+ * finite differences): `record` (N bytes, may be NULL) receives the step's
+ * decisions, `replay` (may be NULL) supplies them instead of the random draws.
+ * Byte j: bit 0 spring j hopped to S+1, bit 1 to S-1, bit 2 attempt j created a
+ * spring at bead 1, bit 3 at bead N, bit 4 old spring j destroyed, bit 5 the
+ * spring of attempt j destroyed. */
+void or_step_chain_tape(const or_params* p, const uint32_t key[2], uint32_t chain_id, uint32_t step,
+                        const double kappa[9], double cd, or_chain* c, or_step_info* info, const uint8_t* replay,
+                        uint8_t* record);
+
 /* Stress of Eq. (stress_tensor_single_chain) and virtual stress of App. B
  * (sum over j = 1..z), both row-major 3x3, in units of kT.  Pinned. */
 void or_stress(const or_params* p, const or_chain* c, double sigma[9], double sigma_v[9]);
@@ -129,10 +139,16 @@ int or_ens_set_flow(or_ens* e, int64_t from_step, const double kappa[9]);
  * S_tr[n_steps][M][z_max] (-1 for empty slots), margin_tr[n_steps][M]. */
 int or_ens_run(or_ens* e, int64_t n_steps, int nthreads, int32_t* Z_tr, int32_t* S_tr,
                double* margin_tr);
+/* or_ens_run with a decision tape [n_steps][M][N]: tape_mode 1 records, 2 replays. */
+int or_ens_run_tape(or_ens* e, int64_t n_steps, int nthreads, int32_t* Z_tr, int32_t* S_tr,
+                    double* margin_tr, uint8_t* tape, int tape_mode);
 void or_ens_get_state(const or_ens* e, double* R, int32_t* Z, int32_t* S, double* A);
 void or_ens_set_state(or_ens* e, const double* R, const int32_t* Z, const int32_t* S,
                       const double* A);
 int64_t or_ens_step(const or_ens* e);
+/* Position the step counter (the Philox counter of the next step); test
+ * support for re-running a window from a saved state with the same noise. */
+void or_ens_set_step(or_ens* e, int64_t step);
 /* correlator group sums acc[G][levels][OR_P][2 channels][3 comps] and the
  * number of samples pushed so far (per chain) */
 void or_ens_corr(const or_ens* e, double* acc, int64_t* n_samples);

@@ -20,7 +20,8 @@ EXPORTS = ["ss_create", "ss_set_params", "ss_set_flow", "ss_run", "ss_stress", "
            "ss_destroy", "ss_last_error", "ss_get_state", "ss_set_state", "ss_step_count",
            "ss_reset_observables", "ss_corr_sums", "ss_log_sums", "ss_counters", "ss_status",
            "ss_synchronize", "ss_run_noalloc", "ss_kernel_timing", "ss_kernel_time",
-           "ss_set_chain_offset", "ss_set_flow_table", "ss_set_batched"]
+           "ss_set_chain_offset", "ss_set_flow_table", "ss_set_batched", "ss_window_forward",
+           "ss_window_backward", "ss_set_coefficients", "ss_set_step_count"]
 
 
 class ss_element(C.Structure):
@@ -76,6 +77,10 @@ def load(path: str = LIB_PATH):
         "ss_set_chain_offset": [vp, C.c_uint32],
         "ss_set_flow_table": [vp, C.c_int, i32p, i64p, dp],
         "ss_set_batched": [vp, C.c_int],
+        "ss_window_forward": [vp, C.c_int64, C.c_int, C.c_int],
+        "ss_window_backward": [vp, dp, dp],
+        "ss_set_coefficients": [vp, C.c_double, C.c_double, C.c_double],
+        "ss_set_step_count": [vp, C.c_int64],
         "ss_kernel_time": [vp, dp, i64p],
         "ss_run_noalloc": [P(ss_params), C.c_int, C.c_uint64, C.c_int32, C.c_int32, C.c_uint32, C.c_int64,
                            C.c_int64, dp, vp, vp, vp, vp, vp, vp, vp],

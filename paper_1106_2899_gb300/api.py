@@ -80,8 +80,30 @@ class SlipSpring:
         """One persistent, graph-replayed launch per chunk over all elements."""
         self._chk(self.lib.ss_set_batched(self.h, 1 if enable else 0), "ss_set_batched")
 
+    def set_coefficients(self, k_b, k_s, zeta):
+        """New (k_b, k_s, zeta) keeping the state, step counter and a recorded window."""
+        self._chk(self.lib.ss_set_coefficients(self.h, float(k_b), float(k_s), float(zeta)), "ss_set_coefficients")
+
     def run(self, n_steps):
         self._chk(self.lib.ss_run(self.h, int(n_steps)), "ss_run")
+
+    # ------------------------------------------------ differentiation ---
+    def window_forward(self, n_steps, checkpoint_every=256, replay=False):
+        """Run a differentiation window (observables reset at its start); with
+        replay the recorded decisions and noise are reused."""
+        self._chk(self.lib.ss_window_forward(self.h, int(n_steps), int(checkpoint_every), 1 if replay else 0),
+                  "ss_window_forward")
+
+    def window_backward(self, dL_dG):
+        """dL/d(k_b, k_s, zeta) from dL/dG [levels][16] of the window's TOTAL channel."""
+        levels = (self.params or {}).get("corr_levels", 0) or 24
+        g = np.ascontiguousarray(dL_dG, dtype=np.float64)
+        if g.shape != (levels, 16):
+            raise ValueError("dL_dG must have shape (%d, 16)" % levels)
+        out = np.zeros(3)
+        self._chk(self.lib.ss_window_backward(self.h, _p(g, C.c_double), _p(out, C.c_double)),
+                  "ss_window_backward")
+        return out
 
     def synchronize(self):
         self._chk(self.lib.ss_synchronize(self.h), "ss_synchronize")
@@ -94,6 +116,11 @@ class SlipSpring:
         s = C.c_int64()
         self._chk(self.lib.ss_step_count(self.h, C.byref(s)), "ss_step_count")
         return s.value
+
+    @step.setter
+    def step(self, value):
+        """Position the step counter (resets the observables)."""
+        self._chk(self.lib.ss_set_step_count(self.h, int(value)), "ss_set_step_count")
 
     # ------------------------------------------------------------ state ---
     def _zm(self, elem):

@@ -18,6 +18,7 @@
 
 #include "slipspring.h"
 #include "ss_kernels.cuh"
+#include "ss_adjoint.cuh"
 
 namespace {
 
@@ -87,6 +88,33 @@ struct ss_ctx {
     std::vector<BatchedClass> bclasses;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
+    // differentiation window
+    struct Window {
+        long long n = 0, t_start = 0;
+        int ce = 0, nseg = 0;
+        bool have_tape = false, forward_done = false;
+        uint8_t* tape = nullptr;
+        void* series = nullptr;
+        void* ckR = nullptr;  // [nseg+1] states
+        void* ckA = nullptr;
+        int32_t* ckS = nullptr;
+        int32_t* ckZ = nullptr;
+        void* snR = nullptr;  // [ce+1] states
+        void* snA = nullptr;
+        int32_t* snS = nullptr;
+        int32_t* snZ = nullptr;
+        void* xbar = nullptr;
+        void* ybar = nullptr;
+        double* scratch = nullptr;
+        void* Rb = nullptr;
+        void* Ab = nullptr;
+        double* grad = nullptr;
+        double* wgt = nullptr;
+    } win;
+    // options of the next chain-kernel launches (set by the window calls)
+    int opt_tape_mode = 0;
+    bool opt_snap = false, opt_series = false, opt_corr_off = false;
+    long long opt_snap_t0 = 0;
     std::string err;
 };
 
@@ -247,6 +275,30 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     a.key1 = (uint32_t)(c->seed >> 32);
     a.chain_base = e.chain_base;
     a.nlog_chunk = p.log_every > 0 ? (int)((t0 + nsteps) / p.log_every - t0 / p.log_every) : 0;
+    if (c->opt_corr_off) {  // recomputation: no observables at all
+        a.levels = 0;
+        a.log_every = 0;
+        a.nlog_chunk = 0;
+    }
+    if (c->opt_tape_mode) {
+        a.tape = c->win.tape;
+        a.tape_mode = c->opt_tape_mode;
+        a.tape_t0 = c->win.t_start;
+        a.tape_rows = c->win.n;
+    }
+    if (c->opt_series) {
+        a.series = c->win.series;
+        a.series_t0 = c->win.t_start;
+        a.series_steps = c->win.n;
+    }
+    if (c->opt_snap) {
+        a.snapR = c->win.snR;
+        a.snapA = c->win.snA;
+        a.snapS = c->win.snS;
+        a.snapZ = c->win.snZ;
+        a.snap_t0 = c->opt_snap_t0;
+        a.snap_steps = c->win.ce;
+    }
     const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, c->Lsm, a.nlog_chunk);
     static int configured_bytes = 0;
     if (plan.total > 48 * 1024 && plan.total > configured_bytes) {
@@ -269,7 +321,7 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         c->events.emplace_back(ev0, ev1);
     }
     c->launches++;
-    if (c->levels > 0) {
+    if (c->levels > 0 && !c->opt_corr_off) {
         const unsigned long long mask = new_sample_levels(c->nsamp, nsteps, c->levels);
         ssk::corr_reduce_kernel<T><<<dim3(e.slices, c->levels), 96, 0, c->stream>>>(
             static_cast<T*>(e.accc), e.acc64, e.M, c->levels, ssk::kSliceChains, mask);
@@ -798,6 +850,141 @@ int batched_run(ss_ctx* c, long long n_steps) {
     return SS_OK;
 }
 
+// ------------------------------------------------------------- window ----
+void free_window(ss_ctx* c) {
+    auto& w = c->win;
+    void* ptrs[] = {w.tape, w.series, w.ckR, w.ckA, w.ckS, w.ckZ, w.snR, w.snA, w.snS, w.snZ,
+                    w.xbar, w.ybar, w.scratch, w.Rb, w.Ab, w.grad, w.wgt};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    w = ss_ctx::Window();
+}
+
+int copy_state(ss_ctx* c, const Elem& e, void* dR, void* dA, int32_t* dS, int32_t* dZ, const void* sR,
+               const void* sA, const int32_t* sS, const int32_t* sZ) {
+    const size_t ts = tsize(c);
+    SS_CUDA(c, cudaMemcpyAsync(dR, sR, (size_t)e.M * 3 * e.NP * ts, cudaMemcpyDeviceToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(dA, sA, (size_t)e.M * 3 * e.NP * ts, cudaMemcpyDeviceToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(dS, sS, (size_t)e.M * e.NP * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(dZ, sZ, (size_t)e.M * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    return SS_OK;
+}
+
+// steps of checkpoint segment seg (the last one may be shorter)
+int seg_len(const ss_ctx* c, int seg) {
+    const long long left = c->win.n - (long long)seg * c->win.ce;
+    return (int)std::min<long long>(c->win.ce, left);
+}
+
+template <typename T, int W, int B>
+int launch_adjoint(ss_ctx* c, Elem& e, int seg) {
+    auto& w = c->win;
+    const size_t ts = sizeof(T);
+    ssk::AdjArgs a{};
+    a.snapR = w.snR;
+    a.snapA = w.snA;
+    a.snapS = w.snS;
+    a.snapZ = w.snZ;
+    a.tape = w.tape + (size_t)seg * w.ce * e.M * e.NP;
+    a.xbar = static_cast<char*>(w.xbar) + (size_t)seg * w.ce * e.M * 3 * ts;
+    a.ybar = static_cast<char*>(w.ybar) + (size_t)seg * w.ce * e.M * 3 * ts;
+    a.Rb = w.Rb;
+    a.Ab = w.Ab;
+    a.grad = w.grad;
+    a.M = e.M;
+    a.N = e.N;
+    a.ns = seg_len(c, seg);
+    a.t0 = w.t_start + (long long)seg * w.ce;
+    a.key0 = (uint32_t)c->seed;
+    a.key1 = (uint32_t)(c->seed >> 32);
+    a.chain_base = e.chain_base;
+    a.destroy_new = c->P.destroy_new;
+    a.create_mode = c->P.create_mode;
+    a.zmax = e.zmax;
+    const int smem = kWarpsPerCta * 32 * B * (int)(2 * sizeof(ssk::Pos<T>) + sizeof(ssk::SlotRec<T>) + 8);
+    if (smem > 48 * 1024)
+        SS_CUDA(c, cudaFuncSetAttribute(ssk::adjoint_kernel<T, W, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int ctas = (e.M + chains_per_cta(W) - 1) / chains_per_cta(W);
+    ssk::adjoint_kernel<T, W, B><<<ctas, kThreads, smem, c->stream>>>(a, step_const<T>(c, e.N));
+    SS_CUDA(c, cudaGetLastError());
+    c->launches++;
+    return SS_OK;
+}
+
+template <typename T>
+int dispatch_adjoint(ss_ctx* c, Elem& e, int seg) {
+    if (e.W == 32) return launch_adjoint<T, 32, 1>(c, e, seg);
+    switch (e.B) {
+        case 1: return launch_adjoint<T, 16, 1>(c, e, seg);
+        case 2: return launch_adjoint<T, 16, 2>(c, e, seg);
+        case 3: return launch_adjoint<T, 16, 3>(c, e, seg);
+        default: return launch_adjoint<T, 16, 4>(c, e, seg);
+    }
+}
+
+template <typename T>
+int window_backward_t(ss_ctx* c, const double* dL_dG, double grad[3]) {
+    auto& w = c->win;
+    Elem& e = c->el[0];
+    const int L = c->levels;
+    const double kT = c->P.kT;
+    // weights of the later x origin products of each (level, lag) slot, TOTAL channel
+    std::vector<double> wg((size_t)L * 16, 0.0);
+    for (int l = 0; l < L; ++l)
+        for (int k = (l == 0 ? 0 : 8); k < 16; ++k) {
+            const long long cnt = std::max(0ll, (w.n >> l) - k);
+            if (cnt > 0 && dL_dG[l * 16 + k] != 0.0)
+                wg[(size_t)l * 16 + k] = dL_dG[l * 16 + k] / (3.0 * e.M * e.N * kT * kT * (double)cnt);
+        }
+    SS_CUDA(c, cudaMemcpyAsync(w.wgt, wg.data(), sizeof(double) * wg.size(), cudaMemcpyHostToDevice, c->stream));
+    {
+        const int thr = 128, n = e.M * 3;
+        ssk::corr_adjoint_kernel<T><<<(n + thr - 1) / thr, thr, 0, c->stream>>>(
+            static_cast<const T*>(w.series), w.n, e.M, L, w.wgt, w.scratch, static_cast<T*>(w.xbar),
+            static_cast<T*>(w.ybar));
+        SS_CUDA(c, cudaGetLastError());
+        c->launches++;
+    }
+    const size_t ts = sizeof(T);
+    SS_CUDA(c, cudaMemsetAsync(w.Rb, 0, (size_t)e.M * 3 * e.NP * ts, c->stream));
+    SS_CUDA(c, cudaMemsetAsync(w.Ab, 0, (size_t)e.M * 3 * e.NP * ts, c->stream));
+    SS_CUDA(c, cudaMemsetAsync(w.grad, 0, (size_t)e.M * 3 * sizeof(double), c->stream));
+    const size_t stR = (size_t)e.M * 3 * e.NP * ts, stS = (size_t)e.M * e.NP * sizeof(int32_t);
+    for (int seg = w.nseg - 1; seg >= 0; --seg) {
+        // recompute the segment from its checkpoint with the recorded decisions,
+        // keeping the state before every step
+        int rc = copy_state(c, e, e.R, e.A, e.S, e.Z, static_cast<char*>(w.ckR) + seg * stR,
+                            static_cast<char*>(w.ckA) + seg * stR,
+                            reinterpret_cast<int32_t*>(reinterpret_cast<char*>(w.ckS) + seg * stS),
+                            w.ckZ + (size_t)seg * e.M);
+        if (rc != SS_OK) return rc;
+        c->opt_tape_mode = 2;
+        c->opt_snap = true;
+        c->opt_corr_off = true;
+        c->opt_snap_t0 = w.t_start + (long long)seg * w.ce;
+        rc = dispatch_chunk<T>(c, e, c->opt_snap_t0, seg_len(c, seg));
+        c->opt_tape_mode = 0;
+        c->opt_snap = false;
+        c->opt_corr_off = false;
+        if (rc != SS_OK) return rc;
+        rc = dispatch_adjoint<T>(c, e, seg);
+        if (rc != SS_OK) return rc;
+    }
+    // the live state is the window's final state again
+    int rc = copy_state(c, e, e.R, e.A, e.S, e.Z, static_cast<char*>(w.ckR) + w.nseg * stR,
+                        static_cast<char*>(w.ckA) + w.nseg * stR,
+                        reinterpret_cast<int32_t*>(reinterpret_cast<char*>(w.ckS) + w.nseg * stS),
+                        w.ckZ + (size_t)w.nseg * e.M);
+    if (rc != SS_OK) return rc;
+    std::vector<double> g((size_t)e.M * 3);
+    SS_CUDA(c, cudaMemcpyAsync(g.data(), w.grad, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    grad[0] = grad[1] = grad[2] = 0.0;
+    for (int m = 0; m < e.M; ++m)
+        for (int k = 0; k < 3; ++k) grad[k] += g[(size_t)m * 3 + k];
+    return SS_OK;
+}
+
 }  // namespace
 
 // ================================================================== C ABI ====
@@ -878,6 +1065,7 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
     if (c->counters) cudaStreamSynchronize(c->stream);
     for (Elem& e : c->el) free_elem(e);
     free_batched(c);
+    free_window(c);
     c->P = p;
     c->k_b = kb;
     c->k_s = ks;
@@ -1086,6 +1274,7 @@ int ss_destroy(ss_ctx* c) {
     }
     for (Elem& e : c->el) free_elem(e);
     free_batched(c);
+    free_window(c);
     if (c->counters) cudaFree(c->counters);
     if (c->status) cudaFree(c->status);
     delete c;
@@ -1150,6 +1339,15 @@ int ss_step_count(ss_ctx* c, int64_t* steps) {
     if (!c || !steps) return SS_EINVAL;
     *steps = c->step;
     return SS_OK;
+}
+
+int ss_set_step_count(ss_ctx* c, int64_t step) {
+    if (!c) return SS_EINVAL;
+    if (!c->have_params) return fail(c, SS_ESTATE, "no parameters");
+    if (step < 0 || step > 0xFFFFFFFFll) return fail(c, SS_EINVAL, "step must be in 0..2^32");
+    if (c->win.forward_done && !c->win.have_tape) return fail(c, SS_ESTATE, "window state inconsistent");
+    c->step = step;
+    return zero_observables(c);
 }
 
 int ss_reset_observables(ss_ctx* c) {
@@ -1239,6 +1437,105 @@ int ss_kernel_time(ss_ctx* c, double* chain_kernel_ms, int64_t* chain_launches) 
     return SS_OK;
 }
 
+
+int ss_window_forward(ss_ctx* c, int64_t n_steps, int checkpoint_every, int replay) {
+    if (!c) return SS_EINVAL;
+    if (!c->have_params) return fail(c, SS_ESTATE, "ss_set_params must precede a window");
+    if (c->el.size() != 1) return fail(c, SS_EINVAL, "a differentiation window needs exactly one element");
+    if (c->levels <= 0) return fail(c, SS_EINVAL, "a differentiation window needs the correlator (corr_levels > 0)");
+    if (c->batched) return fail(c, SS_EINVAL, "a differentiation window runs on the per-element path");
+    if (checkpoint_every < 1 || n_steps < 1) return fail(c, SS_EINVAL, "n_steps, checkpoint_every must be >= 1");
+    if (checkpoint_every > c->P.chunk_steps) return fail(c, SS_EINVAL, "checkpoint_every must be <= chunk_steps");
+    Elem& e = c->el[0];
+    for (double k : e.kap)
+        if (k != 0.0) return fail(c, SS_EINVAL, "differentiation windows run without flow");
+    if (c->step + n_steps > 0xFFFFFFFFll) return fail(c, SS_EOVERFLOW, "step counter would pass 2^32");
+    auto& w = c->win;
+    if (replay && !(w.have_tape && w.n == n_steps && w.ce == checkpoint_every))
+        return fail(c, SS_ESTATE, "replay needs a recorded window of the same length");
+    if (c->P.log_every > 0) {
+        const long long ts = replay ? w.t_start : c->step;
+        if ((ts + n_steps) / c->P.log_every - ts / c->P.log_every > c->P.max_logs)
+            return fail(c, SS_EINVAL, "stress log capacity (max_logs) exceeded");
+    }
+    int rc = upload_flow(c, e);
+    if (rc != SS_OK) return rc;
+    if (!c->initialized) {
+        rc = c->prec == SS_FP64 ? launch_init<double>(c, e) : launch_init<float>(c, e);
+        if (rc != SS_OK) return rc;
+        c->initialized = true;
+    }
+    const size_t ts = tsize(c);
+    const size_t stR = (size_t)e.M * 3 * e.NP * ts, stS = (size_t)e.M * e.NP * sizeof(int32_t);
+    if (!replay) {
+        free_window(c);
+        w.n = n_steps;
+        w.ce = checkpoint_every;
+        w.nseg = (int)((n_steps + checkpoint_every - 1) / checkpoint_every);
+        SS_CUDA(c, cudaMalloc(&w.tape, (size_t)n_steps * e.M * e.NP));
+        SS_CUDA(c, cudaMalloc(&w.series, (size_t)n_steps * e.M * 6 * ts));
+        SS_CUDA(c, cudaMalloc(&w.ckR, (w.nseg + 1) * stR));
+        SS_CUDA(c, cudaMalloc(&w.ckA, (w.nseg + 1) * stR));
+        SS_CUDA(c, cudaMalloc(&w.ckS, (w.nseg + 1) * stS));
+        SS_CUDA(c, cudaMalloc(&w.ckZ, (size_t)(w.nseg + 1) * e.M * sizeof(int32_t)));
+        SS_CUDA(c, cudaMalloc(&w.snR, (size_t)(w.ce + 1) * stR));
+        SS_CUDA(c, cudaMalloc(&w.snA, (size_t)(w.ce + 1) * stR));
+        SS_CUDA(c, cudaMalloc(&w.snS, (size_t)(w.ce + 1) * stS));
+        SS_CUDA(c, cudaMalloc(&w.snZ, (size_t)(w.ce + 1) * e.M * sizeof(int32_t)));
+        SS_CUDA(c, cudaMalloc(&w.xbar, (size_t)n_steps * e.M * 3 * ts));
+        SS_CUDA(c, cudaMalloc(&w.ybar, (size_t)n_steps * e.M * 3 * ts));
+        SS_CUDA(c, cudaMalloc(&w.scratch, (size_t)e.M * 3 * 2 * (n_steps + 1) * sizeof(double)));
+        SS_CUDA(c, cudaMalloc(&w.Rb, stR));
+        SS_CUDA(c, cudaMalloc(&w.Ab, stR));
+        SS_CUDA(c, cudaMalloc(&w.grad, (size_t)e.M * 3 * sizeof(double)));
+        SS_CUDA(c, cudaMalloc(&w.wgt, (size_t)c->levels * 16 * sizeof(double)));
+    }
+    // a replayed window draws the noise of the recorded one: same step indices
+    if (replay) c->step = w.t_start;
+    rc = zero_observables(c);
+    if (rc != SS_OK) return rc;
+    w.t_start = c->step;
+    for (int seg = 0; seg <= w.nseg; ++seg) {
+        rc = copy_state(c, e, static_cast<char*>(w.ckR) + seg * stR, static_cast<char*>(w.ckA) + seg * stR,
+                        reinterpret_cast<int32_t*>(reinterpret_cast<char*>(w.ckS) + seg * stS),
+                        w.ckZ + (size_t)seg * e.M, e.R, e.A, e.S, e.Z);
+        if (rc != SS_OK) return rc;
+        if (seg == w.nseg) break;
+        c->opt_tape_mode = replay ? 2 : 1;
+        c->opt_series = true;
+        const int len = seg_len(c, seg);
+        rc = c->prec == SS_FP64 ? dispatch_chunk<double>(c, e, c->step, len) : dispatch_chunk<float>(c, e, c->step, len);
+        c->opt_tape_mode = 0;
+        c->opt_series = false;
+        if (rc != SS_OK) return rc;
+        c->step += len;
+        c->nsamp += len;
+    }
+    w.have_tape = true;
+    w.forward_done = true;
+    return SS_OK;
+}
+
+int ss_set_coefficients(ss_ctx* c, double k_b, double k_s, double zeta) {
+    if (!c) return SS_EINVAL;
+    if (!c->have_params) return fail(c, SS_ESTATE, "ss_set_params must precede ss_set_coefficients");
+    if (!finite_pos(k_b) || !finite_pos(k_s) || !finite_pos(zeta))
+        return fail(c, SS_EINVAL, "k_b, k_s, zeta must be finite and > 0");
+    if (!(c->P.dt * (4.0 * k_b + k_s) / zeta < 2.0))
+        return fail(c, SS_EINVAL, "Euler step unstable: dt (4 k_b + k_s) / zeta must be < 2");
+    c->k_b = k_b;
+    c->k_s = k_s;
+    c->P.zeta = zeta;
+    c->P.k_b = k_b;
+    c->P.k_s = k_s;
+    return SS_OK;
+}
+
+int ss_window_backward(ss_ctx* c, const double* dL_dG, double grad[3]) {
+    if (!c || !dL_dG || !grad) return SS_EINVAL;
+    if (!c->win.forward_done) return fail(c, SS_ESTATE, "ss_window_forward must precede ss_window_backward");
+    return c->prec == SS_FP64 ? window_backward_t<double>(c, dL_dG, grad) : window_backward_t<float>(c, dL_dG, grad);
+}
 }  // extern "C"
 
 // ====================================================== allocation-free run ===

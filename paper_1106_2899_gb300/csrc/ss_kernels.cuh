@@ -167,7 +167,24 @@ struct ChunkArgs {
     uint32_t key0, key1, chain_base;
     int nlog_chunk;             // log slots reserved in shared memory
     int W, B;                   // lane layout (read by the batched kernel)
+    // differentiation windows (all optional, null when unused):
+    uint8_t* tape;              // [steps][M][NP] decisions per slot and step
+    int tape_mode;              // 0 off, 1 record, 2 replay (decisions frozen)
+    long long tape_t0;          // step of tape row 0
+    long long tape_rows;        // rows of the tape (steps outside are neither read nor written)
+    void* snapR;                // [steps+1][M][3][NP] T: state before each step
+    void* snapA;
+    int32_t* snapS;             // [steps+1][M][NP]
+    int32_t* snapZ;             // [steps+1][M]
+    long long snap_t0;
+    int snap_steps;
+    void* series;               // [steps][M][6] T: sigma_off and sigma_off + sigma^(v)_off after each step
+    long long series_t0;
+    long long series_steps;
 };
+
+// decision byte of one slot in one step (tape): hop, creation, destruction
+constexpr uint8_t kTapeUp = 1, kTapeDown = 2, kTapeNew0 = 4, kTapeNewN = 8, kTapeKillOld = 16, kTapeKillNew = 32;
 
 // One slip-spring slot as the force loop reads it from shared memory:
 // anchor and bead index (-1: empty slot), 16 bytes in FP32.
@@ -326,6 +343,27 @@ __device__ __forceinline__ void corr_level_from_below(const T (&hprev)[3][CPL], 
 // ---------------------------------------------------------- chunk kernel ----
 // W lanes per chain, B beads per lane: bead i and slot i of a chain live on
 // lane i % W as its sub-slot i / W (NP = W*B >= N beads and slots).
+// State of one chain before a step, for the recompute of a differentiation window.
+template <typename T, int W, int B>
+__device__ __forceinline__ void snapshot_store(const ChunkArgs& a, long long row, int mm, int ll, const T (&R)[B][3],
+                                               const T (&A)[B][3], const int (&S)[B], int Z) {
+    constexpr int NP = W * B;
+    T* sR = static_cast<T*>(a.snapR) + ((size_t)row * a.M + mm) * 3 * NP;
+    T* sA = static_cast<T*>(a.snapA) + ((size_t)row * a.M + mm) * 3 * NP;
+    int32_t* sS = a.snapS + ((size_t)row * a.M + mm) * NP;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int i = ll + b * W;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            sR[d * NP + i] = R[b][d];
+            sA[d * NP + i] = i < Z ? A[b][d] : T(0);
+        }
+        sS[i] = i < Z ? S[b] : -1;
+    }
+    if (ll == 0) a.snapZ[(size_t)row * a.M + mm] = Z;
+}
+
 // The chains of one CTA: chains cta_first .. cta_first + chains per CTA - 1 of
 // the element described by `a` (all warps of the CTA call this together).
 template <typename T, int W, int B>
@@ -459,6 +497,16 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             }
             next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
         }
+        if (a.snapR != nullptr && live) {
+            const long long sr = (long long)t0_ + s - a.snap_t0;
+            if (sr >= 0 && sr <= a.snap_steps) snapshot_store<T, W, B>(a, sr, mm, ll, R, A, S, Z);
+        }
+        const long long trow = (long long)t0_ + s - a.tape_t0;
+        const bool tape_row = a.tape_mode != 0 && live && trow >= 0 && trow < a.tape_rows;
+        uint8_t tb[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            tb[b] = (a.tape_mode == 2 && tape_row) ? a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] : (uint8_t)0;
         // ---- slot table and per-bead slot masks for this step's spring forces
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -597,8 +645,13 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             const T dm = rm[0] * rm[0] + rm[1] * rm[1] + rm[2] * rm[2];
             const T pp = (si < N - 1) ? hop_prob_fast<T>(c, dp, d0) : T(0);
             const T pm = (si > 0) ? hop_prob_fast<T>(c, dm, d0) : T(0);
-            const bool up = occ && (u[b] < pp);
-            const bool dn = occ && !up && (u[b] < pp + pm);
+            bool up = occ && (u[b] < pp);
+            bool dn = occ && !up && (u[b] < pp + pm);
+            if (a.tape_mode == 2) {
+                up = occ && (tb[b] & kTapeUp);
+                dn = occ && (tb[b] & kTapeDown);
+            }
+            if (a.tape_mode == 1) tb[b] |= (up ? kTapeUp : 0) | (dn ? kTapeDown : 0);
             S[b] = up ? si + 1 : (dn ? si - 1 : S[b]);
             cnt_up += up ? 1u : 0u;
             cnt_dn += dn ? 1u : 0u;
@@ -618,6 +671,8 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             const int i = ll + b * W;
             const bool att = (i >= first) && (i < last);
             end_new[b] = !att ? -1 : (u[b] < pc ? 0 : (u[b] < T(2) * pc ? N - 1 : -1));
+            if (a.tape_mode == 2) end_new[b] = !att ? -1 : ((tb[b] & kTapeNew0) ? 0 : ((tb[b] & kTapeNewN) ? N - 1 : -1));
+            if (a.tape_mode == 1) tb[b] |= end_new[b] == 0 ? kTapeNew0 : (end_new[b] > 0 ? kTapeNewN : 0);
             any_new |= end_new[b] >= 0;
         }
         T Anew[B][3];
@@ -648,8 +703,16 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
             const bool hit = nrm[b][3] < c.cd;
-            const bool kill_old = (i < Zc) && (S[b] == 0 || S[b] == N - 1) && hit;
-            const bool kill_new = (end_new[b] >= 0) && a.destroy_new && hit;
+            bool kill_old = (i < Zc) && (S[b] == 0 || S[b] == N - 1) && hit;
+            bool kill_new = (end_new[b] >= 0) && a.destroy_new && hit;
+            if (a.tape_mode == 2) {
+                kill_old = (i < Zc) && (tb[b] & kTapeKillOld);
+                kill_new = (end_new[b] >= 0) && (tb[b] & kTapeKillNew);
+            }
+            if (a.tape_mode == 1) {
+                tb[b] |= (kill_old ? kTapeKillOld : 0) | (kill_new ? kTapeKillNew : 0);
+                if (tape_row) a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] = tb[b];
+            }
             alive_old[b] = (i < Zc) && !kill_old;
             alive_new[b] = (end_new[b] >= 0) && !kill_new;
             cnt_de += (kill_old ? 1u : 0u) + (kill_new ? 1u : 0u);
@@ -754,6 +817,17 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             for (int d = 0; d < 3; ++d) {
                 sig[d] = shfl(red, d * G8, W);
                 tot[d] = shfl(red, (3 + d) * G8, W);
+            }
+            if (a.series != nullptr && live && ll == 0) {
+                const long long sr = (long long)t0_ + s - a.series_t0;
+                if (sr >= 0 && sr < a.series_steps) {
+                    T* out = static_cast<T*>(a.series) + ((size_t)sr * a.M + mm) * 6;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        out[d] = sig[d];
+                        out[3 + d] = tot[d];
+                    }
+                }
             }
             if (do_log) {
                 T dg[3];
@@ -864,6 +938,11 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             }
         }
         __syncwarp();
+    }
+
+    if (a.snapR != nullptr && live) {
+        const long long sr = (long long)t0_ + nsteps_ - a.snap_t0;
+        if (sr >= 0 && sr <= a.snap_steps) snapshot_store<T, W, B>(a, sr, mm, ll, R, A, S, Z);
     }
 
     // ---- store state
