@@ -300,11 +300,14 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         a.snap_steps = c->win.ce;
     }
     const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, c->Lsm, a.nlog_chunk);
-    static int configured_bytes = 0;
-    if (plan.total > 48 * 1024 && plan.total > configured_bytes) {
-        SS_CUDA(c, cudaFuncSetAttribute(ssk::chunk_kernel<T, W, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        plan.total));
-        configured_bytes = plan.total;
+    // differentiation windows run the instantiation with the window hooks
+    const bool win = c->opt_tape_mode != 0 || c->opt_snap || c->opt_series;
+    void (*kern)(const ssk::ChunkArgs, const ssk::StepConst<T>) =
+        win ? ssk::chunk_kernel<T, W, B, true> : ssk::chunk_kernel<T, W, B, false>;
+    static int configured_bytes[2] = {0, 0};
+    if (plan.total > 48 * 1024 && plan.total > configured_bytes[win]) {
+        SS_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
+        configured_bytes[win] = plan.total;
     }
     const ssk::StepConst<T> sc = step_const<T>(c, e.N);
     const int ctas = (e.M + chains_per_cta(W) - 1) / chains_per_cta(W);
@@ -314,7 +317,7 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         SS_CUDA(c, cudaEventCreate(&ev1));
         SS_CUDA(c, cudaEventRecord(ev0, c->stream));
     }
-    ssk::chunk_kernel<T, W, B><<<ctas, kThreads, plan.total, c->stream>>>(a, sc);
+    kern<<<ctas, kThreads, plan.total, c->stream>>>(a, sc);
     SS_CUDA(c, cudaGetLastError());
     if (c->timing) {
         SS_CUDA(c, cudaEventRecord(ev1, c->stream));
@@ -1614,7 +1617,7 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
     a.nlog_chunk = 0;
     const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, c->Lsm, 0);
     if (plan.total > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(ssk::chunk_kernel<T, W, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(ssk::chunk_kernel<T, W, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              plan.total);
         if (e != cudaSuccess) return SS_ECUDA;
     }
@@ -1625,7 +1628,7 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
         a.t0 = t0 + done;
         a.nsteps = ns;
         a.nsamp0 = done;
-        ssk::chunk_kernel<T, W, B><<<(M + chains_per_cta(W) - 1) / chains_per_cta(W), kThreads, plan.total, st>>>(a, sc);
+        ssk::chunk_kernel<T, W, B, false><<<(M + chains_per_cta(W) - 1) / chains_per_cta(W), kThreads, plan.total, st>>>(a, sc);
         if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
         if (c->levels > 0) {
             ssk::corr_reduce_kernel<T><<<dim3(a.slices, c->levels), 96, 0, st>>>(

@@ -366,7 +366,7 @@ __device__ __forceinline__ void snapshot_store(const ChunkArgs& a, long long row
 
 // The chains of one CTA: chains cta_first .. cta_first + chains per CTA - 1 of
 // the element described by `a` (all warps of the CTA call this together).
-template <typename T, int W, int B>
+template <typename T, int W, int B, bool WIN>
 __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T>& c, const int cta_first,
                                            const T NkT, const long long t0_, const int nsteps_,
                                            const long long log_m0_, const int nlog_) {
@@ -388,6 +388,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     const int mm = live ? m : 0;
     const uint32_t chain_id = a.chain_base + (uint32_t)mm;
     const int N = a.N;
+    const int tmode = WIN ? a.tape_mode : 0;  // differentiation windows only
     const unsigned segmask = (W == 32) ? kFull : (((1u << W) - 1u) << (seg * W));
     const unsigned lt = ((1u << lane) - 1u) & segmask;  // lanes of this segment below this one
 
@@ -497,16 +498,16 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             }
             next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
         }
-        if (a.snapR != nullptr && live) {
+        if (WIN && a.snapR != nullptr && live) {
             const long long sr = (long long)t0_ + s - a.snap_t0;
             if (sr >= 0 && sr <= a.snap_steps) snapshot_store<T, W, B>(a, sr, mm, ll, R, A, S, Z);
         }
         const long long trow = (long long)t0_ + s - a.tape_t0;
-        const bool tape_row = a.tape_mode != 0 && live && trow >= 0 && trow < a.tape_rows;
+        const bool tape_row = WIN && tmode != 0 && live && trow >= 0 && trow < a.tape_rows;
         uint8_t tb[B];
 #pragma unroll
         for (int b = 0; b < B; ++b)
-            tb[b] = (a.tape_mode == 2 && tape_row) ? a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] : (uint8_t)0;
+            tb[b] = (tmode == 2 && tape_row) ? a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] : (uint8_t)0;
         // ---- slot table and per-bead slot masks for this step's spring forces
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -647,11 +648,11 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             const T pm = (si > 0) ? hop_prob_fast<T>(c, dm, d0) : T(0);
             bool up = occ && (u[b] < pp);
             bool dn = occ && !up && (u[b] < pp + pm);
-            if (a.tape_mode == 2) {
+            if (tmode == 2) {
                 up = occ && (tb[b] & kTapeUp);
                 dn = occ && (tb[b] & kTapeDown);
             }
-            if (a.tape_mode == 1) tb[b] |= (up ? kTapeUp : 0) | (dn ? kTapeDown : 0);
+            if (tmode == 1) tb[b] |= (up ? kTapeUp : 0) | (dn ? kTapeDown : 0);
             S[b] = up ? si + 1 : (dn ? si - 1 : S[b]);
             cnt_up += up ? 1u : 0u;
             cnt_dn += dn ? 1u : 0u;
@@ -671,8 +672,8 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             const int i = ll + b * W;
             const bool att = (i >= first) && (i < last);
             end_new[b] = !att ? -1 : (u[b] < pc ? 0 : (u[b] < T(2) * pc ? N - 1 : -1));
-            if (a.tape_mode == 2) end_new[b] = !att ? -1 : ((tb[b] & kTapeNew0) ? 0 : ((tb[b] & kTapeNewN) ? N - 1 : -1));
-            if (a.tape_mode == 1) tb[b] |= end_new[b] == 0 ? kTapeNew0 : (end_new[b] > 0 ? kTapeNewN : 0);
+            if (tmode == 2) end_new[b] = !att ? -1 : ((tb[b] & kTapeNew0) ? 0 : ((tb[b] & kTapeNewN) ? N - 1 : -1));
+            if (tmode == 1) tb[b] |= end_new[b] == 0 ? kTapeNew0 : (end_new[b] > 0 ? kTapeNewN : 0);
             any_new |= end_new[b] >= 0;
         }
         T Anew[B][3];
@@ -705,11 +706,11 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             const bool hit = nrm[b][3] < c.cd;
             bool kill_old = (i < Zc) && (S[b] == 0 || S[b] == N - 1) && hit;
             bool kill_new = (end_new[b] >= 0) && a.destroy_new && hit;
-            if (a.tape_mode == 2) {
+            if (tmode == 2) {
                 kill_old = (i < Zc) && (tb[b] & kTapeKillOld);
                 kill_new = (end_new[b] >= 0) && (tb[b] & kTapeKillNew);
             }
-            if (a.tape_mode == 1) {
+            if (tmode == 1) {
                 tb[b] |= (kill_old ? kTapeKillOld : 0) | (kill_new ? kTapeKillNew : 0);
                 if (tape_row) a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] = tb[b];
             }
@@ -818,7 +819,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 sig[d] = shfl(red, d * G8, W);
                 tot[d] = shfl(red, (3 + d) * G8, W);
             }
-            if (a.series != nullptr && live && ll == 0) {
+            if (WIN && a.series != nullptr && live && ll == 0) {
                 const long long sr = (long long)t0_ + s - a.series_t0;
                 if (sr >= 0 && sr < a.series_steps) {
                     T* out = static_cast<T*>(a.series) + ((size_t)sr * a.M + mm) * 6;
@@ -940,7 +941,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         __syncwarp();
     }
 
-    if (a.snapR != nullptr && live) {
+    if (WIN && a.snapR != nullptr && live) {
         const long long sr = (long long)t0_ + nsteps_ - a.snap_t0;
         if (sr >= 0 && sr <= a.snap_steps) snapshot_store<T, W, B>(a, sr, mm, ll, R, A, S, Z);
     }
@@ -1026,10 +1027,12 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     }
 }
 
-template <typename T, int W, int B>
+// WIN: the differentiation-window hooks (decision tape, snapshots, stress
+// series) are compiled in; the plain kernel carries none of them.
+template <typename T, int W, int B, bool WIN>
 __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_MULTI)
     chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
-    run_chains<T, W, B>(a, c, blockIdx.x * (kChunkThreads / W), c.NkT, a.t0, a.nsteps, a.log_m0, a.nlog_chunk);
+    run_chains<T, W, B, WIN>(a, c, blockIdx.x * (kChunkThreads / W), c.NkT, a.t0, a.nsteps, a.log_m0, a.nlog_chunk);
 }
 
 // ------------------------------------------------------ batched kernel ------
@@ -1059,7 +1062,7 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
         const int2 wi = items[it];
         const ChunkArgs& a = elems[wi.x];
         const int nlog = a.log_every > 0 ? (int)((info.t0 + info.nsteps) / a.log_every - info.t0 / a.log_every) : 0;
-        run_chains<T, W, B>(a, c, wi.y, T((double)a.N) * c.kT, info.t0, info.nsteps, info.log_m0, nlog);
+        run_chains<T, W, B, false>(a, c, wi.y, T((double)a.N) * c.kT, info.t0, info.nsteps, info.log_m0, nlog);
     }
 }
 
