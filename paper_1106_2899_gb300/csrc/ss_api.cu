@@ -24,8 +24,6 @@ namespace {
 
 constexpr int kThreads = ssk::kChunkThreads;
 constexpr int kWarpsPerCta = kThreads / 32;
-constexpr int kCorrSmemBudget = 48 * 1024;  // bytes of shared memory for correlator levels
-constexpr int kMaxSmemLevels = 7;
 
 struct Elem {
     int M = 0, N = 0, W = 16, B = 2, NP = 32, zmax = 0;
@@ -35,10 +33,11 @@ struct Elem {
     void* A = nullptr;
     int32_t* S = nullptr;
     int32_t* Z = nullptr;
-    void* hist = nullptr;
-    void* histg = nullptr;
-    void* accc = nullptr;
-    double* acc64 = nullptr;
+    void* hist = nullptr;    // [M][L][6][16] T: newest 16 samples per correlator level and series row
+    double* acc64 = nullptr;  // [slices][L][96] FP64 sums
+    void* ser = nullptr;     // [ser_cap][M][6] T: stress series of one launch
+    void* lev = nullptr;     // [2][ser_cap / 2 + 1][M][6] T: correlator level samples (ping-pong)
+    int ser_cap = 0;
     double* logs = nullptr;
     double* kap_d = nullptr;
     long long* kfrom_d = nullptr;
@@ -69,7 +68,7 @@ struct ss_ctx {
     bool have_params = false;
     bool initialized = false;
     double k_b = 0, k_s = 0;
-    int levels = 0, Lsm = 0;
+    int levels = 0;
     long long step = 0;
     long long nsamp = 0;
     long long log_m0 = 0;
@@ -136,10 +135,11 @@ int fail(ss_ctx* c, int code, const std::string& msg) {
 size_t tsize(const ss_ctx* c) { return c->prec == SS_FP64 ? sizeof(double) : sizeof(float); }
 
 void free_elem(Elem& e) {
-    void* ptrs[] = {e.R, e.A, e.S, e.Z, e.hist, e.histg, e.accc, e.acc64, e.logs, e.kap_d, e.kfrom_d};
+    void* ptrs[] = {e.R, e.A, e.S, e.Z, e.hist, e.acc64, e.ser, e.lev, e.logs, e.kap_d, e.kfrom_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    e.R = e.A = e.hist = e.histg = e.accc = nullptr;
+    e.R = e.A = e.hist = e.ser = e.lev = nullptr;
+    e.ser_cap = 0;
     e.S = e.Z = nullptr;
     e.acc64 = e.logs = e.kap_d = nullptr;
     e.kfrom_d = nullptr;
@@ -166,26 +166,6 @@ void layout_for(int N, int* W, int* B) {
 }
 
 int chains_per_cta(int W) { return kWarpsPerCta * (32 / W); }
-
-// correlator levels kept in shared memory (after the register levels)
-int smem_levels(const ss_ctx* c, int W) {
-    const int beyond = c->levels - 1 - ssk::kRegLevels;
-    if (beyond <= 0) return 0;
-    const int per_level = chains_per_cta(W) * 2 * 3 * ssk::kCells * (int)tsize(c);
-    return std::max(0, std::min({beyond, kMaxSmemLevels, kCorrSmemBudget / per_level}));
-}
-
-// Correlator levels that receive a sample among samples n0+1 .. n0+ns.
-unsigned long long new_sample_levels(long long n0, long long ns, int L) {
-    unsigned long long mask = 0;
-    for (int l = 0; l < L && l < 63; ++l)
-        if (((n0 + ns) >> l) > (n0 >> l)) mask |= 1ull << l;
-    return mask;
-}
-
-// levels stored between launches (registers + shared memory) and in global memory
-int saved_levels(const ss_ctx* c) { return 1 + ssk::kRegLevels + c->Lsm; }
-int global_levels(const ss_ctx* c) { return std::max(0, c->levels - saved_levels(c)); }
 
 // Inverse standard normal CDF by bisection on erfc: the destruction
 // threshold on a standard normal draw (host constant).
@@ -238,6 +218,38 @@ ssk::StepConst<T> step_const(const ss_ctx* c, int N) {
     return s;
 }
 
+// Correlator kernels of one launch: level 0 on the launch's series (ns rows
+// of [M][6]), then one kernel per higher level that completes a sample; each
+// CTA folds its slice's sums into acc64.  n0: samples before the launch; lev:
+// two level-sample buffers of lev_half elements.  Returns the number of
+// kernels launched, or -1.
+template <typename T>
+int corr_launches(const T* ser, int ns, int M, int L, long long n0, T* hist, double* acc64, T* lev,
+                  size_t lev_half, cudaStream_t st) {
+    auto cl_of = [&](int l) { return (int)(((n0 + ns) >> l) - (n0 >> l)); };
+    int launches = 0;
+    const int grid = (M + ssk::kSliceChains - 1) / ssk::kSliceChains;
+    const int last0 = (L == 1 || cl_of(1) == 0) ? 1 : 0;
+    ssk::corr_level0_kernel<T><<<grid, ssk::kCorrThreads, 0, st>>>(ser, ns, M, L, hist, acc64, last0);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    ++launches;
+    const T* yin = ser;
+    int cprev = ns;
+    for (int l = 1; l < L; ++l) {
+        const int cl = cl_of(l);
+        if (cl == 0) break;
+        T* yout = lev + (size_t)((l - 1) & 1) * lev_half;
+        const int last = (l == L - 1 || cl_of(l + 1) == 0) ? 1 : 0;
+        ssk::corr_level_kernel<T><<<grid, ssk::kCorrThreads, 0, st>>>(yin, cprev, n0 >> (l - 1), n0 >> l, cl, l, M,
+                                                                     L, hist, yout, acc64, last);
+        if (cudaGetLastError() != cudaSuccess) return -1;
+        ++launches;
+        yin = yout;
+        cprev = cl;
+    }
+    return launches;
+}
+
 template <typename T, int W, int B>
 int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     const ss_params& p = c->P;
@@ -246,9 +258,6 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     a.A = e.A;
     a.S = e.S;
     a.Z = e.Z;
-    a.hist = e.hist;
-    a.histg = e.histg;
-    a.accc = e.accc;
     a.logs = e.logs;
     a.counters = c->counters;
     a.status = c->status;
@@ -260,8 +269,6 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     a.zmax = e.zmax;
     a.create_mode = p.create_mode;
     a.destroy_new = p.destroy_new;
-    a.levels = c->levels;
-    a.Lsm = c->Lsm;
     a.log_every = p.log_every;
     a.recenter_every = p.recenter_every;
     a.log_m0 = c->log_m0;
@@ -270,13 +277,24 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     a.slices = e.slices;
     a.t0 = t0;
     a.nsteps = nsteps;
-    a.nsamp0 = c->nsamp;
     a.key0 = (uint32_t)c->seed;
     a.key1 = (uint32_t)(c->seed >> 32);
     a.chain_base = e.chain_base;
     a.nlog_chunk = p.log_every > 0 ? (int)((t0 + nsteps) / p.log_every - t0 / p.log_every) : 0;
+    // the correlator's input: this launch's stress series (a window keeps the
+    // series of the whole window for its adjoint)
+    const bool corr = c->levels > 0 && !c->opt_corr_off;
+    if (corr && nsteps > ssk::kCorrMaxSteps) return fail(c, SS_EINVAL, "launch longer than the correlator accepts");
+    if (corr) {
+        if (c->opt_series) {
+            a.series = c->win.series;
+            a.series_row0 = t0 - c->win.t_start;
+        } else {
+            a.series = e.ser;
+            a.series_row0 = 0;
+        }
+    }
     if (c->opt_corr_off) {  // recomputation: no observables at all
-        a.levels = 0;
         a.log_every = 0;
         a.nlog_chunk = 0;
     }
@@ -286,11 +304,6 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         a.tape_t0 = c->win.t_start;
         a.tape_rows = c->win.n;
     }
-    if (c->opt_series) {
-        a.series = c->win.series;
-        a.series_t0 = c->win.t_start;
-        a.series_steps = c->win.n;
-    }
     if (c->opt_snap) {
         a.snapR = c->win.snR;
         a.snapA = c->win.snA;
@@ -299,9 +312,9 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         a.snap_t0 = c->opt_snap_t0;
         a.snap_steps = c->win.ce;
     }
-    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, c->Lsm, a.nlog_chunk);
+    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, a.nlog_chunk);
     // differentiation windows run the instantiation with the window hooks
-    const bool win = c->opt_tape_mode != 0 || c->opt_snap || c->opt_series;
+    const bool win = c->opt_tape_mode != 0 || c->opt_snap;
     void (*kern)(const ssk::ChunkArgs, const ssk::StepConst<T>) =
         win ? ssk::chunk_kernel<T, W, B, true> : ssk::chunk_kernel<T, W, B, false>;
     static int configured_bytes[2] = {0, 0};
@@ -324,12 +337,12 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         c->events.emplace_back(ev0, ev1);
     }
     c->launches++;
-    if (c->levels > 0 && !c->opt_corr_off) {
-        const unsigned long long mask = new_sample_levels(c->nsamp, nsteps, c->levels);
-        ssk::corr_reduce_kernel<T><<<dim3(e.slices, c->levels), 96, 0, c->stream>>>(
-            static_cast<T*>(e.accc), e.acc64, e.M, c->levels, ssk::kSliceChains, mask);
-        SS_CUDA(c, cudaGetLastError());
-        c->launches++;
+    if (corr) {
+        const T* ser = static_cast<const T*>(a.series) + (size_t)a.series_row0 * e.M * 6;
+        const int nl = corr_launches<T>(ser, nsteps, e.M, c->levels, c->nsamp, static_cast<T*>(e.hist), e.acc64,
+                                        static_cast<T*>(e.lev), (size_t)(e.ser_cap / 2 + 1) * e.M * 6, c->stream);
+        if (nl < 0) return fail(c, SS_ECUDA, "correlator kernel launch failed");
+        c->launches += nl;
     }
     return SS_OK;
 }
@@ -397,10 +410,7 @@ int upload_flow(ss_ctx* c, Elem& e) {
 int zero_observables(ss_ctx* c) {
     const size_t ts = tsize(c);
     for (Elem& e : c->el) {
-        const int Lg = global_levels(c);
-        if (e.hist) SS_CUDA(c, cudaMemsetAsync(e.hist, 0, (size_t)e.M * saved_levels(c) * 96 * ts, c->stream));
-        if (e.histg && Lg > 0) SS_CUDA(c, cudaMemsetAsync(e.histg, 0, (size_t)e.M * Lg * 96 * ts, c->stream));
-        if (e.accc) SS_CUDA(c, cudaMemsetAsync(e.accc, 0, (size_t)e.M * c->levels * 96 * ts, c->stream));
+        if (e.hist) SS_CUDA(c, cudaMemsetAsync(e.hist, 0, (size_t)e.M * c->levels * 96 * ts, c->stream));
         if (e.acc64)
             SS_CUDA(c, cudaMemsetAsync(e.acc64, 0, (size_t)e.slices * c->levels * 96 * sizeof(double), c->stream));
         if (e.logs && c->P.max_logs > 0)
@@ -551,8 +561,6 @@ ssk::ChunkArgs make_desc(const ss_ctx* c, const Elem& e) {
     a.zmax = e.zmax;
     a.create_mode = p.create_mode;
     a.destroy_new = p.destroy_new;
-    a.levels = 0;
-    a.Lsm = 0;
     a.log_every = p.log_every;
     a.recenter_every = p.recenter_every;
     a.max_logs = p.max_logs;
@@ -602,7 +610,7 @@ const void* batched_fn_of(int k) {
 template <typename T>
 int batched_smem_bytes(const ss_ctx* c, int k) {
     const int nlog = c->P.log_every > 0 ? c->P.chunk_steps / c->P.log_every + 1 : 0;
-    return ssk::smem_plan<T>(kWarpsPerCta, kLayoutW[k], kLayoutB[k], 0, nlog).total;
+    return ssk::smem_plan<T>(kWarpsPerCta, kLayoutW[k], kLayoutB[k], nlog).total;
 }
 
 // persistent grid size of class k: resident CTAs per SM x SMs, at most one per item
@@ -1075,11 +1083,9 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
     c->levels = p.corr_levels > 0 ? p.corr_levels : 0;
     c->step = 0;
     c->initialized = false;
-    int Lsm_all = kMaxSmemLevels;
-    for (const Elem& e : c->el) Lsm_all = std::min(Lsm_all, smem_levels(c, e.W));
-    c->Lsm = Lsm_all;
+    // with the correlator on, a launch covers at most kCorrMaxSteps steps
+    if (c->levels > 0) c->P.chunk_steps = std::min(c->P.chunk_steps, ssk::kCorrMaxSteps);
     const size_t ts = tsize(c);
-    const int Lg = global_levels(c);
     for (Elem& e : c->el) {
         e.zmax = p.z_max > 0 ? p.z_max : e.N;
         e.slices = (e.M + ssk::kSliceChains - 1) / ssk::kSliceChains;
@@ -1090,9 +1096,10 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
         SS_CUDA(c, cudaMalloc(&e.Z, (size_t)e.M * sizeof(int32_t)));
         SS_CUDA(c, cudaMemsetAsync(e.Z, 0, (size_t)e.M * sizeof(int32_t), c->stream));
         if (c->levels > 0) {
-            SS_CUDA(c, cudaMalloc(&e.hist, (size_t)e.M * saved_levels(c) * 96 * ts));
-            if (Lg > 0) SS_CUDA(c, cudaMalloc(&e.histg, (size_t)e.M * Lg * 96 * ts));
-            SS_CUDA(c, cudaMalloc(&e.accc, (size_t)e.M * c->levels * 96 * ts));
+            SS_CUDA(c, cudaMalloc(&e.hist, (size_t)e.M * c->levels * 96 * ts));
+            e.ser_cap = c->P.chunk_steps;
+            SS_CUDA(c, cudaMalloc(&e.ser, (size_t)e.M * 6 * e.ser_cap * ts));
+            SS_CUDA(c, cudaMalloc(&e.lev, (size_t)2 * (e.ser_cap / 2 + 1) * e.M * 6 * ts));
             SS_CUDA(c, cudaMalloc(&e.acc64, (size_t)e.slices * c->levels * 96 * sizeof(double)));
         }
         if (p.max_logs > 0) SS_CUDA(c, cudaMalloc(&e.logs, (size_t)p.max_logs * e.groups * 14 * sizeof(double)));
@@ -1582,16 +1589,13 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 template <typename T, int W, int B>
 int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint32_t chain_base, int64_t t0,
                      int64_t n_steps, void* R, void* A, int32_t* S, int32_t* Z, unsigned char* scr,
-                     size_t off_hist, size_t off_histg, size_t off_accc, size_t off_acc64, size_t off_kap,
+                     size_t off_hist, size_t off_ser, size_t off_lev, int ser_cap, size_t off_acc64, size_t off_kap,
                      size_t off_kfrom, size_t off_cnt, size_t off_status, cudaStream_t st) {
     ssk::ChunkArgs a{};
     a.R = R;
     a.A = A;
     a.S = S;
     a.Z = Z;
-    a.hist = scr + off_hist;
-    a.histg = scr + off_histg;
-    a.accc = scr + off_accc;
     a.logs = nullptr;
     a.counters = reinterpret_cast<unsigned long long*>(scr + off_cnt);
     a.status = reinterpret_cast<int32_t*>(scr + off_status);
@@ -1603,8 +1607,6 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
     a.zmax = zmax;
     a.create_mode = p.create_mode;
     a.destroy_new = p.destroy_new;
-    a.levels = c->levels;
-    a.Lsm = c->Lsm;
     a.log_every = 0;
     a.recenter_every = p.recenter_every;
     a.log_m0 = 0;
@@ -1615,7 +1617,11 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
     a.key1 = (uint32_t)(c->seed >> 32);
     a.chain_base = chain_base;
     a.nlog_chunk = 0;
-    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, c->Lsm, 0);
+    if (c->levels > 0) {
+        a.series = scr + off_ser;
+        a.series_row0 = 0;
+    }
+    const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, 0);
     if (plan.total > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(ssk::chunk_kernel<T, W, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              plan.total);
@@ -1624,18 +1630,16 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
     const ssk::StepConst<T> sc = step_const<T>(c, N);
     int64_t done = 0;
     while (done < n_steps) {
-        const int ns = (int)std::min<int64_t>(n_steps - done, p.chunk_steps);
+        const int ns = (int)std::min<int64_t>(n_steps - done, c->levels > 0 ? ser_cap : p.chunk_steps);
         a.t0 = t0 + done;
         a.nsteps = ns;
-        a.nsamp0 = done;
         ssk::chunk_kernel<T, W, B, false><<<(M + chains_per_cta(W) - 1) / chains_per_cta(W), kThreads, plan.total, st>>>(a, sc);
         if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
-        if (c->levels > 0) {
-            ssk::corr_reduce_kernel<T><<<dim3(a.slices, c->levels), 96, 0, st>>>(
-                static_cast<T*>(a.accc), reinterpret_cast<double*>(scr + off_acc64), M, c->levels,
-                ssk::kSliceChains, new_sample_levels(done, ns, c->levels));
-            if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
-        }
+        if (c->levels > 0 &&
+            corr_launches<T>(static_cast<const T*>(a.series), ns, M, c->levels, done,
+                             reinterpret_cast<T*>(scr + off_hist), reinterpret_cast<double*>(scr + off_acc64),
+                             reinterpret_cast<T*>(scr + off_lev), (size_t)(ser_cap / 2 + 1) * M * 6, st) < 0)
+            return SS_ECUDA;
         done += ns;
     }
     return SS_OK;
@@ -1696,21 +1700,15 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
         c.k_b = kb;
         c.k_s = ks;
         c.levels = q.corr_levels > 0 ? q.corr_levels : 0;
-        c.Lsm = smem_levels(&c, e.W);
+        if (c.levels > 0) c.P.chunk_steps = std::min(c.P.chunk_steps, ssk::kCorrMaxSteps);
         c.el[0].zmax = zm;
     }
     // scratch layout
     const size_t ts = tsize(&c);
-    const int W = e.W;
     const int slices = (n_chains + ssk::kSliceChains - 1) / ssk::kSliceChains;
-    const int Lsave = saved_levels(&c), Lg = global_levels(&c);
     const bool corr = c.levels > 0;
     size_t off = 0;
     const size_t off_hist = off;
-    off = align256(off + (corr ? (size_t)n_chains * Lsave * 96 * ts : 0));
-    const size_t off_histg = off;
-    off = align256(off + (corr ? (size_t)n_chains * Lg * 96 * ts : 0));
-    const size_t off_accc = off;
     off = align256(off + (corr ? (size_t)n_chains * c.levels * 96 * ts : 0));
     const size_t off_acc64 = off;
     off = align256(off + (corr ? (size_t)slices * c.levels * 96 * sizeof(double) : 0));
@@ -1723,13 +1721,30 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
     const size_t off_status = off;
     off = align256(off + sizeof(int32_t));
     if (off > (size_t)SS_NOALLOC_SCRATCH_BYTES) return SS_ETOOBIG;
+    // the stress series of one launch and the correlator's level samples take
+    // the rest: (cap + 2 (cap / 2 + 1)) rows of [M][6], cap <= chunk_steps
+    const size_t off_ser = off;
+    int ser_cap = 0;
+    size_t off_lev = off;
+    if (corr) {
+        const size_t row = (size_t)n_chains * 6 * ts;
+        const size_t rows = ((size_t)SS_NOALLOC_SCRATCH_BYTES - off) / row;  // >= 2 cap + 2 needed
+        ser_cap = (int)std::min<size_t>(c.P.chunk_steps, rows >= 2 ? (rows - 2) / 2 : 0);
+        if (ser_cap < 1) return SS_ETOOBIG;
+        off_lev = align256(off_ser + (size_t)ser_cap * row);
+        if (off_lev + (size_t)2 * (ser_cap / 2 + 1) * row > (size_t)SS_NOALLOC_SCRATCH_BYTES) {
+            ser_cap -= 1;  // the alignment pad
+            off_lev = align256(off_ser + (size_t)ser_cap * row);
+            if (ser_cap < 1) return SS_ETOOBIG;
+        }
+    }
 
     unsigned char* scr = nullptr;
     int rc = noalloc_scratch(&scr);
     if (rc != SS_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    // what must start at zero: history, partial sums, counters, status
-    if (cudaMemsetAsync(scr, 0, off, st) != cudaSuccess) return SS_ECUDA;
+    // what must start at zero: history, sums, counters, status (not the series)
+    if (cudaMemsetAsync(scr, 0, off_ser, st) != cudaSuccess) return SS_ECUDA;
     double kap_h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (kappa) std::memcpy(kap_h, kappa, sizeof(kap_h));
     // a copy from pageable host memory is staged before cudaMemcpyAsync returns,
@@ -1738,8 +1753,8 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
         return SS_ECUDA;
     const int zm = c.el[0].zmax;
 #define SS_NOALLOC_ARGS                                                                                          \
-    &c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A, S, Z, scr, off_hist, off_histg, off_accc,    \
-        off_acc64, off_kap, off_kfrom, off_cnt, off_status, st
+    &c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A, S, Z, scr, off_hist, off_ser, off_lev,       \
+        ser_cap, off_acc64, off_kap, off_kfrom, off_cnt, off_status, st
     if (precision == SS_FP64) {
         if (e.W == 32) rc = noalloc_launches<double, 32, 1>(SS_NOALLOC_ARGS);
         else if (e.B == 1) rc = noalloc_launches<double, 16, 1>(SS_NOALLOC_ARGS);

@@ -1,6 +1,6 @@
 // ss_kernels.cuh -- sm_103a kernels of the single-chain slip-spring time step
-// (T. Uneyama, arXiv:1106.2899, Sec. 3.1), with stress sampling into a
-// multiple-tau correlator and ensemble stress logs.
+// (T. Uneyama, arXiv:1106.2899, Sec. 3.1), with a per-step stress series
+// for the multiple-tau correlator (a separate kernel) and ensemble stress logs.
 //
 // Layout: one chain per W-lane segment of a warp (W = 32: one chain per warp,
 // W = 16: two), B beads per lane: lane l of a segment owns beads and
@@ -22,7 +22,7 @@
 namespace ssk {
 
 constexpr int kP = 16;      // multiple-tau points per level
-constexpr int kCells = 32;  // (channel, lag) cells per level: channel*16 + lag
+constexpr int kCells = 32;  // (channel, lag) cells per level and component: channel*16 + lag
 constexpr uint32_t kPurposeStep = 1, kPurposeCreate = 2, kPurposeInitBond = 3,
                    kPurposeInitZ = 4, kPurposeInitS = 5, kPurposeInitA = 6;
 constexpr unsigned kFull = 0xffffffffu;
@@ -145,11 +145,6 @@ struct ChunkArgs {
     void* A;            // [M][3][W] T
     int32_t* S;         // [M][W]
     int32_t* Z;         // [M]
-    void* hist;         // [M][1+kRegLevels+Lsm][3][32] T: levels kept between launches
-    void* histg;        // [M][Lg][3][32] T: the levels beyond those
-    void* accc;         // [M][L][3][32] T: each chain's correlator sums of this launch
-                        // (levels kept on chip are stored at the end, the others
-                        // accumulate here); a reduce kernel folds them into acc64
     double* logs;       // [max_logs][groups][14]
     unsigned long long* counters;  // [8]
     int32_t* status;
@@ -157,13 +152,11 @@ struct ChunkArgs {
     const long long* kap_from;  // [n_kap]
     int n_kap;
     int M, N, zmax, create_mode, destroy_new;
-    int levels, Lsm;            // correlator levels (0: off); levels in shared memory
     int log_every, recenter_every;
     long long log_m0;           // logs are taken at steps m*log_every with m > log_m0
     int max_logs, groups, slices;  // slices of kSliceChains chains
     long long t0;               // first step index of this launch
     int nsteps;
-    long long nsamp0;           // correlator samples per chain before this launch
     uint32_t key0, key1, chain_base;
     int nlog_chunk;             // log slots reserved in shared memory
     int W, B;                   // lane layout (read by the batched kernel)
@@ -178,9 +171,11 @@ struct ChunkArgs {
     int32_t* snapZ;             // [steps+1][M]
     long long snap_t0;
     int snap_steps;
-    void* series;               // [steps][M][6] T: sigma_off and sigma_off + sigma^(v)_off after each step
-    long long series_t0;
-    long long series_steps;
+    // stress series for the correlator (null: not written): element
+    // [((series_row0 + s) * M + m) * 6 + q] is, after step s of this launch,
+    // sigma_off (q = 0..2: xy, xz, yz) or (sigma + sigma^(v))_off (q = 3..5)
+    void* series;
+    long long series_row0;
 };
 
 // decision byte of one slot in one step (tape): hop, creation, destruction
@@ -200,29 +195,25 @@ struct __align__(16) Pos {
     T x, y, z, w;
 };
 
-// correlator levels kept in registers (levels 0..kRegLevels)
-#ifndef SS_REG_LEVELS
-#define SS_REG_LEVELS 2
-#endif
-constexpr int kRegLevels = SS_REG_LEVELS;
-
 // threads per CTA of the chunk kernel, and resident CTAs per SM it is compiled for
 constexpr int kChunkThreads = 128;
 #ifndef SS_CTAS_PER_SM
 #define SS_CTAS_PER_SM 6
 #endif
 #ifndef SS_CTAS_PER_SM_MULTI
-#define SS_CTAS_PER_SM_MULTI 4  // for layouts with several beads per lane
+#define SS_CTAS_PER_SM_MULTI 5  // for layouts with several beads per lane
+#endif
+#ifndef SS_CTAS_PER_SM_BATCHED_MULTI
+#define SS_CTAS_PER_SM_BATCHED_MULTI 4  // the batched kernel reads its arguments through a pointer
 #endif
 
 // shared memory carve-up (bytes), identical on host and device
 struct SmemPlan {
-    int off_tab, off_pos, off_msk, off_log, off_corr, off_red, total;
+    int off_tab, off_pos, off_msk, off_log, total;
 };
 
 template <typename T>
-__host__ __device__ inline SmemPlan smem_plan(int warps, int W, int B, int Lsm, int nlog_chunk) {
-    const int chains = warps * (32 / W);
+__host__ __device__ inline SmemPlan smem_plan(int warps, int W, int B, int nlog_chunk) {
     SmemPlan p;
     p.off_tab = 0;
     int sz = warps * 32 * B * (int)sizeof(SlotRec<T>);
@@ -232,9 +223,7 @@ __host__ __device__ inline SmemPlan smem_plan(int warps, int W, int B, int Lsm, 
     sz = p.off_msk + warps * 32 * B * (int)sizeof(unsigned long long);
     p.off_log = (sz + 15) & ~15;
     sz = p.off_log + nlog_chunk * 14 * (int)sizeof(double);
-    p.off_corr = (sz + 15) & ~15;
-    sz = p.off_corr + chains * Lsm * 2 * 3 * kCells * (int)sizeof(T);
-    p.off_red = p.total = (sz + 15) & ~15;
+    p.total = (sz + 15) & ~15;
     return p;
 }
 
@@ -315,31 +304,6 @@ __device__ __forceinline__ float hop_prob_fast<float>(const StepConst<float>& c,
     return fminf(c.two_pref * r, 0.5f);
 }
 
-// One multiple-tau level update of the lane's CPL cells.  hprev holds the
-// (already updated) cells of the level below; the new sample of this level is
-// the mean of the two newest samples below (its lag-0 and lag-1 cells), which
-// enters at lag 0 of each channel; the lag products use the new sample of the
-// AUTO channel (sigma) as the later value.  Cells of lags below P/2 are
-// accumulated too and ignored on readout for levels >= 1.
-template <typename T, int W, int CPL>
-__device__ __forceinline__ void corr_level_from_below(const T (&hprev)[3][CPL], T (&h)[3][CPL],
-                                                      T (&acc)[3][CPL], int ll) {
-    const bool lag0 = (ll & 15) == 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        T v[CPL];
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) v[k] = T(0.5) * (hprev[c][k] + __shfl_down_sync(kFull, hprev[c][k], 1, 16));
-        const T x = shfl(v[0], 0, W);
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) {
-            const T hs = __shfl_up_sync(kFull, h[c][k], 1, 16);
-            h[c][k] = lag0 ? v[k] : hs;
-            acc[c][k] += x * h[c][k];
-        }
-    }
-}
-
 // ---------------------------------------------------------- chunk kernel ----
 // W lanes per chain, B beads per lane: bead i and slot i of a chain live on
 // lane i % W as its sub-slot i / W (NP = W*B >= N beads and slots).
@@ -372,8 +336,6 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                                            const long long log_m0_, const int nlog_) {
     constexpr int SEGS = 32 / W;
     constexpr int NP = W * B;
-    constexpr int CPL = kCells / W;  // correlator cells per lane
-    constexpr int LR = kRegLevels;
     constexpr int G8 = W / 8;        // lanes per value group after seg_reduce8
     using Mask = unsigned long long;
     const int lane = threadIdx.x & 31;
@@ -381,7 +343,6 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     const int nwarps = blockDim.x >> 5;
     const int seg = lane / W;
     const int ll = lane % W;
-    const int cpc = nwarps * SEGS;  // chains per CTA
     const int cslot = warp * SEGS + seg;
     const int m = cta_first + cslot;
     const bool live = m < a.M;
@@ -393,12 +354,11 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     const unsigned lt = ((1u << lane) - 1u) & segmask;  // lanes of this segment below this one
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemPlan plan = smem_plan<T>(nwarps, W, B, a.Lsm, nlog_);
+    const SmemPlan plan = smem_plan<T>(nwarps, W, B, nlog_);
     SlotRec<T>* tab = reinterpret_cast<SlotRec<T>*>(smem + plan.off_tab) + (warp * SEGS + seg) * NP;
     Pos<T>* pos = reinterpret_cast<Pos<T>*>(smem + plan.off_pos) + (warp * SEGS + seg) * NP;
     Mask* msk = reinterpret_cast<Mask*>(smem + plan.off_msk) + (warp * SEGS + seg) * NP;
     double* slog = reinterpret_cast<double*>(smem + plan.off_log);
-    T* scorr = reinterpret_cast<T*>(smem + plan.off_corr);
 
     for (int i = threadIdx.x; i < nlog_ * 14; i += blockDim.x) slog[i] = 0.0;
 
@@ -425,38 +385,14 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         pos[i] = p0;
     }
 
-    // ---- correlator: levels 0..LR in registers, LR+1..LR+Lsm in shared
-    // memory, the rest in global memory; the sums restart at every launch
-    const bool corr_on = a.levels > 0;
-    const int Lsave = 1 + LR + a.Lsm;  // levels stored in a.hist between launches
-    const int Lglob = a.levels - Lsave;
-    T hr[LR + 1][3][CPL], ar[LR + 1][3][CPL];
-    const T* Hs = static_cast<const T*>(a.hist);
-#pragma unroll
-    for (int l = 0; l <= LR; ++l)
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int k = 0; k < CPL; ++k) {
-                const int cell = k * W + ll;
-                hr[l][d][k] = (corr_on && live && l < a.levels)
-                                  ? Hs[(((size_t)mm * Lsave + l) * 3 + d) * kCells + cell] : T(0);
-                ar[l][d][k] = T(0);
-            }
-    if (corr_on) {
-        for (int l = 0; l < a.Lsm; ++l) {
-            T* base = scorr + ((size_t)(cslot * a.Lsm + l) * 2) * 96;
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-                for (int k = 0; k < CPL; ++k) {
-                    const int cell = k * W + ll;
-                    base[d * kCells + cell] =
-                        live ? Hs[(((size_t)mm * Lsave + LR + 1 + l) * 3 + d) * kCells + cell] : T(0);
-                    base[96 + d * kCells + cell] = T(0);
-                }
-        }
-    }
+    // stress series of this launch (the correlator reads it afterwards)
+    T* const ser = static_cast<T*>(a.series);
+    const bool corr_on = ser != nullptr;
+    const int gq = ll / G8;  // value this lane holds after seg_reduce8
+    T* const ser_m = (corr_on && live && (ll % G8) == 0 && gq < 6)
+                         ? ser + ((size_t)a.series_row0 * a.M + mm) * 6 + gq
+                         : nullptr;
+    const size_t ser_step = (size_t)a.M * 6;
     if (nlog_ > 0)
         __syncthreads();  // the CTA's stress-log buffer is zeroed
     else
@@ -482,7 +418,6 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     int next_rc = a.recenter_every > 0 ? rel((t0_ / a.recenter_every + 1) * a.recenter_every - 1) : never;
     int log_slot = 0;
     const uint32_t t0lo = (uint32_t)t0_;
-    const uint32_t n0lo = (uint32_t)a.nsamp0;
 
     unsigned cnt_up = 0, cnt_dn = 0, cnt_cr = 0, cnt_de = 0, cnt_drop = 0;
 
@@ -813,27 +748,14 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             v[4] += v[1];
             v[5] += v[2];
             const T red = seg_reduce8<T, W>(v, ll);
-            T sig[3], tot[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                sig[d] = shfl(red, d * G8, W);
-                tot[d] = shfl(red, (3 + d) * G8, W);
-            }
-            if (WIN && a.series != nullptr && live && ll == 0) {
-                const long long sr = (long long)t0_ + s - a.series_t0;
-                if (sr >= 0 && sr < a.series_steps) {
-                    T* out = static_cast<T*>(a.series) + ((size_t)sr * a.M + mm) * 6;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        out[d] = sig[d];
-                        out[3 + d] = tot[d];
-                    }
-                }
-            }
+            if (ser_m != nullptr) ser_m[(size_t)s * ser_step] = red;  // the correlator's input
             if (do_log) {
-                T dg[3];
+                T sig[3], dg[3];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) dg[d] = seg_sum<T, W>(dgp[d]) - NkT;
+                for (int d = 0; d < 3; ++d) {
+                    sig[d] = shfl(red, d * G8, W);
+                    dg[d] = seg_sum<T, W>(dgp[d]) - NkT;
+                }
                 const int slot = log_slot++;
                 if (live && ll == 0 && slot < nlog_) {
                     double* L = slog + slot * 14;
@@ -846,69 +768,6 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                     }
                     atomicAdd(L + 12, (double)Z);
                     atomicAdd(L + 13, (double)Z * (double)Z);
-                }
-            }
-            if (corr_on) {
-                const uint32_t n = n0lo + (uint32_t)s + 1u;  // samples after this one
-                const bool lag0 = (ll & 15) == 0;
-                // level 0: every step
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-#pragma unroll
-                    for (int k = 0; k < CPL; ++k) {
-                        const int cell = k * W + ll;
-                        const T ins = (cell >> 4) ? tot[d] : sig[d];
-                        const T hs = __shfl_up_sync(kFull, hr[0][d][k], 1, 16);
-                        hr[0][d][k] = lag0 ? ins : hs;
-                        ar[0][d][k] += sig[d] * hr[0][d][k];
-                    }
-                // register levels: level l when n is a multiple of 2^l
-#pragma unroll
-                for (int l = 1; l <= LR; ++l) {
-                    if (l < a.levels && (n & ((1u << l) - 1u)) == 0u)
-                        corr_level_from_below<T, W, CPL>(hr[l - 1], hr[l], ar[l], ll);
-                }
-                // shared and global levels
-                if (LR + 1 < a.levels && (n & ((1u << (LR + 1)) - 1u)) == 0u) {
-                    T hprev[3][CPL];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d)
-#pragma unroll
-                        for (int k = 0; k < CPL; ++k) hprev[d][k] = hr[LR][d][k];
-                    for (int l = LR + 1; l < a.levels; ++l) {
-                        if (l < 32 && (n & ((1u << l) - 1u)) != 0u) break;
-                        T h[3][CPL], ac[3][CPL];
-                        T* hb;
-                        T* ab;
-                        if (l < Lsave) {
-                            hb = scorr + ((size_t)(cslot * a.Lsm + (l - LR - 1)) * 2) * 96;
-                            ab = hb + 96;
-                        } else {
-                            hb = static_cast<T*>(a.histg) + ((size_t)mm * Lglob + (l - Lsave)) * 96;
-                            ab = static_cast<T*>(a.accc) + ((size_t)mm * a.levels + l) * 96;
-                        }
-#pragma unroll
-                        for (int d = 0; d < 3; ++d)
-#pragma unroll
-                            for (int k = 0; k < CPL; ++k) {
-                                h[d][k] = hb[d * kCells + k * W + ll];
-                                ac[d][k] = ab[d * kCells + k * W + ll];
-                            }
-                        corr_level_from_below<T, W, CPL>(hprev, h, ac, ll);
-                        if (live || l < Lsave) {
-#pragma unroll
-                            for (int d = 0; d < 3; ++d)
-#pragma unroll
-                                for (int k = 0; k < CPL; ++k) {
-                                    hb[d * kCells + k * W + ll] = h[d][k];
-                                    ab[d * kCells + k * W + ll] = ac[d][k];
-                                }
-                        }
-#pragma unroll
-                        for (int d = 0; d < 3; ++d)
-#pragma unroll
-                            for (int k = 0; k < CPL; ++k) hprev[d][k] = h[d][k];
-                    }
                 }
             }
         }
@@ -984,33 +843,6 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         }
     }
 
-    // ---- correlator: save the stored levels, store this launch's sums per chain
-    if (corr_on && live) {
-        T* Hw = static_cast<T*>(a.hist);
-        T* C = static_cast<T*>(a.accc) + (size_t)mm * a.levels * 96;
-#pragma unroll
-        for (int l = 0; l <= LR; ++l) {
-            if (l >= a.levels) break;
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-                for (int k = 0; k < CPL; ++k) {
-                    Hw[(((size_t)mm * Lsave + l) * 3 + d) * kCells + k * W + ll] = hr[l][d][k];
-                    C[(size_t)l * 96 + d * kCells + k * W + ll] = ar[l][d][k];
-                }
-        }
-        for (int l = 0; l < a.Lsm; ++l) {
-            const T* base = scorr + ((size_t)(cslot * a.Lsm + l) * 2) * 96;
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-                for (int k = 0; k < CPL; ++k) {
-                    Hw[(((size_t)mm * Lsave + LR + 1 + l) * 3 + d) * kCells + k * W + ll] = base[d * kCells + k * W + ll];
-                    C[(size_t)(LR + 1 + l) * 96 + d * kCells + k * W + ll] = base[96 + d * kCells + k * W + ll];
-                }
-        }
-    }
-
     // ---- stress logs: add this CTA's sums to its group
     if (a.log_every > 0 && nlog_ > 0) {
         __syncthreads();
@@ -1049,7 +881,7 @@ struct RunInfo {
 };
 
 template <typename T, int W, int B>
-__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_MULTI)
+__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_BATCHED_MULTI)
     batched_kernel(const ChunkArgs* __restrict__ elems, const int2* __restrict__ items, int n_items,
                    unsigned* __restrict__ next_item, const RunInfo info, const StepConst<T> c) {
     __shared__ int item_s;
@@ -1066,24 +898,197 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
     }
 }
 
-// ---------------------------------------------------------- reduce kernel ----
-// Folds the chains' correlator sums of one launch into FP64 slice sums:
-// acc64[s][l][i] += sum over the chains of slice s, in chain order, of
-// accc[m][l][i]; accc is zeroed for the next launch.  Levels without a new
-// sample in the launch are skipped (their sums are zero).  Grid: (slices, L).
+// ----------------------------------------------------- correlator kernels ----
+// Multiple-tau lag products of one launch's stress series (Eq.
+// relaxation_modulus_tensor_green_kubo_form, App. B).  Level 0 holds the raw
+// samples; level l >= 1 the means of two consecutive level-(l-1) samples, i.e.
+// of blocks of 2^l raw samples aligned to the absolute sample index.  At level
+// l, lag k (0..15 at level 0, 8..15 above) adds x_l(j) y_l(j - k) for every
+// sample j completed in this launch, with x = sigma_off (the later value) and
+// y = sigma_off (AUTO channel) or (sigma + sigma^(v))_off (TOTAL channel).
+//
+// One thread per (chain, series row q): q = 0..2 are sigma_off (xy, xz, yz),
+// q = 3..5 (sigma + sigma^(v))_off; a warp holds 5 chains x 6 rows, and the
+// later value x of row q is row q % 3 of the same chain, taken by a shuffle.
+// Samples of a level are [j][M][6] arrays (the chain kernel's series for
+// level 0).  hist [M][L][6][16] keeps the newest 16 samples of every level
+// and row (oldest first, zero after a reset): the lags reach back into
+// earlier launches through a 16-entry register ring.  Level l's kernel also
+// brings level l-1's history up to date (it needs the old newest sample of
+// level l-1 for a pair that straddles the launch boundary); the kernel of the
+// last level with new samples updates its own.  A CTA covers one slice of
+// kSliceChains chains and adds its chains' sums of this launch, in chain
+// order, to the slice's FP64 sums acc64 [slices][L][3][32] (component,
+// channel * 16 + lag).
+constexpr int kCorrChainsPerWarp = 5;
+constexpr int kCorrWarps = (kSliceChains + kCorrChainsPerWarp - 1) / kCorrChainsPerWarp;  // 13
+constexpr int kCorrThreads = kCorrWarps * 32;
+constexpr int kCorrMaxSteps = 1024;  // samples per launch (the level-sample buffers hold half)
+
+// This slice's FP32 sums of one level (each thread's lags k0..15 of its row),
+// folded in chain order into FP64.
 template <typename T>
-__global__ void corr_reduce_kernel(T* __restrict__ accc, double* __restrict__ acc64, int M, int L,
-                                   int slice_chains, unsigned long long level_mask) {
-    const int sl = blockIdx.x, l = blockIdx.y, i = threadIdx.x;
-    if (i >= 96 || !((level_mask >> l) & 1ull)) return;
-    const int m0 = sl * slice_chains, m1 = min(M, m0 + slice_chains);
-    double sum = 0.0;
-    for (int m = m0; m < m1; ++m) {
-        T* p = accc + ((size_t)m * L + l) * 96 + i;
-        sum += (double)*p;
-        *p = T(0);
+__device__ __forceinline__ void corr_fold_slice(const T (&acc)[16], int k0, bool live, int slot, int q,
+                                                double* __restrict__ out, T* red) {
+    // red: [kSliceChains][96] T in shared memory
+    if (slot < kSliceChains) {
+        T* row = red + (size_t)slot * 96 + (q % 3) * kCells + (q / 3) * kP;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k >= k0) row[k] = live ? acc[k] : T(0);
     }
-    acc64[((size_t)sl * L + l) * 96 + i] += sum;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 96; i += blockDim.x) {
+        const int lag = i % kP;
+        if (lag < k0) continue;
+        double sum = 0.0;
+        for (int c = 0; c < kSliceChains; ++c) sum += (double)red[(size_t)c * 96 + i];
+        out[i] += sum;
+    }
+}
+
+// Ring of the newest 16 samples of one row: r[i] holds sample base + i - 16
+// when the next sample to enter is sample base (i.e. after a whole number of
+// 16-sample blocks).  Products of n new samples y (with later values x).
+// Products of n new samples, sample j given by get(j) (a load, or a pair mean
+// that is also stored for the next level); nr returns the ring position of
+// the next sample (the number of samples in the last partial block).
+template <typename T, int K0, typename Get>
+__device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], Get get, int n, int src_lane, int& nr) {
+    int j = 0;
+    for (; j + 16 <= n; j += 16) {
+        T yv[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) yv[u] = get(j + u);  // independent loads first
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const T xv = __shfl_sync(kFull, yv[u], src_lane);
+            r[u] = yv[u];
+#pragma unroll
+            for (int k = K0; k < 16; ++k) acc[k] += xv * r[(u - k) & 15];
+        }
+    }
+    const int rem = n - j;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        if (u < rem) {
+            const T yv = get(j + u);
+            const T xv = __shfl_sync(kFull, yv, src_lane);
+            r[u] = yv;
+#pragma unroll
+            for (int k = K0; k < 16; ++k) acc[k] += xv * r[(u - k) & 15];
+        }
+    }
+    nr = rem;
+}
+
+// The newest 16 samples in ring order after `nr` samples of a partial block:
+// out[i] = r[(nr + i) & 15].
+template <typename T>
+__device__ __forceinline__ void corr_ring_newest(const T (&r)[16], int nr, T* out) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        T v = r[0];
+#pragma unroll
+        for (int s2 = 1; s2 < 16; ++s2)
+            if (((nr + i) & 15) == s2) v = r[s2];
+        out[i] = v;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCorrThreads)
+    corr_level0_kernel(const T* __restrict__ ser, int ns, int M, int L, T* __restrict__ hist,
+                       double* __restrict__ acc64, int last) {
+    __shared__ T red[kSliceChains * 96];
+    const int lane = threadIdx.x & 31;
+    const int cc = lane / 6, q = lane % 6;
+    const int slot = (threadIdx.x >> 5) * kCorrChainsPerWarp + cc;  // chain within the slice
+    const int m = blockIdx.x * kSliceChains + slot;
+    const bool live = lane < 30 && slot < kSliceChains && m < M;
+    const int mm = live ? m : 0;
+    const int src_lane = cc * 6 + q % 3;
+    T* h = hist + (((size_t)mm * L) * 6 + q) * 16;
+    T r[16], acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        r[i] = live ? h[i] : T(0);
+        acc[i] = T(0);
+    }
+    int nr = 0;
+    const T* yrow = ser + (size_t)mm * 6 + q;
+    const size_t stride = (size_t)M * 6;
+    corr_ring_products<T, 0>(r, acc, [&](int j) { return yrow[(size_t)j * stride]; }, ns, min(src_lane, 31), nr);
+    corr_fold_slice(acc, 0, live, lane < 30 ? slot : kSliceChains, q, acc64 + ((size_t)blockIdx.x * L) * 96, red);
+    if (!live) return;
+    if (last) {
+        T nh[16];
+        corr_ring_newest(r, nr, nh);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = nh[i];
+    }
+}
+
+// Level l >= 1 from the cprev level-(l-1) samples of this launch, yin
+// [cprev][M][6] (absolute indices pb .. pb + cprev - 1); writes the cl new
+// level-l samples to yout [cl][M][6] (absolute indices nb ..).
+template <typename T>
+__global__ void __launch_bounds__(kCorrThreads)
+    corr_level_kernel(const T* __restrict__ yin, int cprev, long long pb, long long nb, int cl, int l, int M,
+                      int L, T* __restrict__ hist, T* __restrict__ yout, double* __restrict__ acc64, int last) {
+    __shared__ T red[kSliceChains * 96];
+    const int lane = threadIdx.x & 31;
+    const int cc = lane / 6, q = lane % 6;
+    const int slot = (threadIdx.x >> 5) * kCorrChainsPerWarp + cc;
+    const int m = blockIdx.x * kSliceChains + slot;
+    const bool live = lane < 30 && slot < kSliceChains && m < M;
+    const int mm = live ? m : 0;
+    const int src_lane = min(cc * 6 + q % 3, 31);
+    const size_t stride = (size_t)M * 6;
+    // level l-1: its newest sample before this launch, then its history brought up to date
+    T* hp = hist + (((size_t)mm * L + (l - 1)) * 6 + q) * 16;
+    T old[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) old[i] = live ? hp[i] : T(0);
+    const T* yrow = yin + (size_t)mm * 6 + q;
+    if (live) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int src = cprev - 16 + i;  // position among the new samples
+            hp[i] = src >= 0 ? yrow[(size_t)src * stride] : old[cprev + i];
+        }
+    }
+    // level l samples: pairs (2J, 2J+1) of level l-1, the first possibly
+    // straddling the launch boundary; stored for level l+1 as they are made
+    const int off = (int)(2 * nb - pb);  // -1 or 0
+    const T pend = old[15];
+    T* orow = yout + (size_t)mm * 6 + q;
+    auto mean = [&](int j) {
+        const int a0 = off + 2 * j;
+        const T v0 = a0 >= 0 ? yrow[(size_t)a0 * stride] : pend;
+        const T v = T(0.5) * (v0 + yrow[(size_t)(a0 + 1) * stride]);
+        if (live) orow[(size_t)j * stride] = v;
+        return v;
+    };
+    // lag products of level l over its new samples
+    T* h = hist + (((size_t)mm * L + l) * 6 + q) * 16;
+    T r[16], acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        r[i] = live ? h[i] : T(0);
+        acc[i] = T(0);
+    }
+    int nr = 0;
+    corr_ring_products<T, kP / 2>(r, acc, mean, cl, src_lane, nr);
+    corr_fold_slice(acc, kP / 2, live, lane < 30 ? slot : kSliceChains, q,
+                    acc64 + ((size_t)blockIdx.x * L + l) * 96, red);
+    if (!live) return;
+    if (last) {
+        T nh[16];
+        corr_ring_newest(r, nr, nh);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = nh[i];
+    }
 }
 
 // ------------------------------------------------------------ init kernel ----
