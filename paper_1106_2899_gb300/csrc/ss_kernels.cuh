@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace ssk {
 
 constexpr int kP = 16;      // multiple-tau points per level
@@ -216,7 +218,8 @@ template <typename T>
 __host__ __device__ inline SmemPlan smem_plan(int warps, int W, int B, int nlog_chunk) {
     SmemPlan p;
     p.off_tab = 0;
-    int sz = warps * 32 * B * (int)sizeof(SlotRec<T>);
+    // per chain NP slot records and one record of zeros that empty gathers read
+    int sz = warps * (32 / W) * (W * B + 1) * (int)sizeof(SlotRec<T>);
     p.off_pos = (sz + 15) & ~15;
     sz = p.off_pos + warps * 32 * B * (int)sizeof(Pos<T>);
     p.off_msk = (sz + 15) & ~15;
@@ -228,6 +231,10 @@ __host__ __device__ inline SmemPlan smem_plan(int warps, int W, int B, int nlog_
 }
 
 // -------------------------------------------------------------- helpers -----
+// 1 + index of the lowest set bit (0 for none) of a 32- or 64-bit slot mask
+__device__ __forceinline__ int mask_ffs(unsigned m) { return __ffs((int)m); }
+__device__ __forceinline__ int mask_ffs(unsigned long long m) { return __ffsll((long long)m); }
+
 // Sum over the W lanes of a segment; every lane of the segment gets the sum.
 template <typename T, int W>
 __device__ __forceinline__ T seg_sum(T v) {
@@ -337,7 +344,8 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     constexpr int SEGS = 32 / W;
     constexpr int NP = W * B;
     constexpr int G8 = W / 8;        // lanes per value group after seg_reduce8
-    using Mask = unsigned long long;
+    // per-bead slot masks: 32 bits cover every slot when NP <= 32
+    using Mask = typename std::conditional<(NP <= 32), unsigned, unsigned long long>::type;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -355,7 +363,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemPlan plan = smem_plan<T>(nwarps, W, B, nlog_);
-    SlotRec<T>* tab = reinterpret_cast<SlotRec<T>*>(smem + plan.off_tab) + (warp * SEGS + seg) * NP;
+    SlotRec<T>* tab = reinterpret_cast<SlotRec<T>*>(smem + plan.off_tab) + (warp * SEGS + seg) * (NP + 1);
     Pos<T>* pos = reinterpret_cast<Pos<T>*>(smem + plan.off_pos) + (warp * SEGS + seg) * NP;
     Mask* msk = reinterpret_cast<Mask*>(smem + plan.off_msk) + (warp * SEGS + seg) * NP;
     double* slog = reinterpret_cast<double*>(smem + plan.off_log);
@@ -421,6 +429,29 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 
     unsigned cnt_up = 0, cnt_dn = 0, cnt_cr = 0, cnt_de = 0, cnt_drop = 0;
 
+    // slot table: anchors (and bead indices) of the slots; kept current by the
+    // re-indexing below, and rewritten every step only while a flow moves anchors
+    auto write_tab = [&]() {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+            SlotRec<T> rec;
+            rec.x = A[b][0];
+            rec.y = A[b][1];
+            rec.z = A[b][2];
+            rec.s = i < Z ? S[b] : -1;
+            tab[i] = rec;
+        }
+    };
+    write_tab();
+    bool tab_dirty = false;  // anchors moved (flow, recentring) since the table was written
+    if (ll == 0) {
+        SlotRec<T> zero;
+        zero.x = zero.y = zero.z = T(0);
+        zero.s = -1;
+        tab[NP] = zero;
+    }
+
     for (int s = 0; s < nsteps_; ++s) {
         const uint32_t t = t0lo + (uint32_t)s;
         if (s >= next_from) {
@@ -444,17 +475,12 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         for (int b = 0; b < B; ++b)
             tb[b] = (tmode == 2 && tape_row) ? a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] : (uint8_t)0;
         // ---- slot table and per-bead slot masks for this step's spring forces
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const int i = ll + b * W;
-            SlotRec<T> rec;
-            rec.x = A[b][0];
-            rec.y = A[b][1];
-            rec.z = A[b][2];
-            rec.s = i < Z ? S[b] : -1;
-            tab[i] = rec;
-            msk[i] = 0ull;
+        if (tab_dirty) {
+            write_tab();
+            tab_dirty = false;
         }
+#pragma unroll
+        for (int b = 0; b < B; ++b) msk[ll + b * W] = Mask(0);
         // ---- random numbers of this step: block (i, t, STEP, chain) per bead/slot i
         T nrm[B][4], u[B];
 #pragma unroll
@@ -468,7 +494,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
-            if (i < Z) atomicOr(&msk[S[b]], 1ull << i);
+            if (i < Z) atomicOr(&msk[S[b]], Mask(1) << i);
         }
 
         // ---- substep 1: forces at time t, Euler-Maruyama, anchor advection
@@ -493,20 +519,17 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             // springs on this bead: k_s (sum_j A_j - n R), slots in ascending order
-            Mask mb = msk[ll + b * W];
-            T sx = T(0), sy = T(0), sz = T(0), cnt = T(0);
-#pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                const bool has = mb != 0ull;
-                const SlotRec<T> r = tab[has ? __ffsll((long long)mb) - 1 : 0];
-                mb &= mb - 1ull;
-                sx += has ? r.x : T(0);
-                sy += has ? r.y : T(0);
-                sz += has ? r.z : T(0);
-                cnt += has ? T(1) : T(0);
-            }
+            // (an empty mask reads the zero record at NP)
+            const Mask m0 = msk[ll + b * W];
+            const Mask m1 = m0 & (m0 - Mask(1));
+            const int j0 = m0 ? mask_ffs(m0) - 1 : NP;
+            const int j1 = m1 ? mask_ffs(m1) - 1 : NP;
+            const SlotRec<T> r0 = tab[j0], r1 = tab[j1];
+            const T sx = r0.x + r1.x, sy = r0.y + r1.y, sz = r0.z + r1.z;
+            const T cnt = T((m0 != Mask(0)) + (m1 != Mask(0)));
+            const Mask mb = m1 & (m1 - Mask(1));
             mrest[b] = mb;
-            more |= mb != 0ull;
+            more |= mb != Mask(0);
             F[b][0] += c.k_s * (sx - cnt * R[b][0]);
             F[b][1] += c.k_s * (sy - cnt * R[b][1]);
             F[b][2] += c.k_s * (sz - cnt * R[b][2]);
@@ -518,8 +541,8 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 Mask mb = mrest[b];
                 T sx = T(0), sy = T(0), sz = T(0), cnt = T(0);
                 while (mb) {
-                    const SlotRec<T> r = tab[__ffsll((long long)mb) - 1];
-                    mb &= mb - 1ull;
+                    const SlotRec<T> r = tab[mask_ffs(mb) - 1];
+                    mb &= mb - Mask(1);
                     sx += r.x;
                     sy += r.y;
                     sz += r.z;
@@ -541,6 +564,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d]) : T(0);
             }
             if (kap_nz && i < Z) {
+                tab_dirty = true;
                 T An[3];
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
@@ -780,6 +804,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             T com[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) com[d] = seg_sum<T, W>(csum[d]) / T(N);
+            tab_dirty = true;
             __syncwarp();
 #pragma unroll
             for (int b = 0; b < B; ++b) {
