@@ -67,6 +67,51 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint
     return make_uint4(c0, c1, c2, c3);
 }
 
+// The same generator for the step draws of a fixed (index, purpose, chain):
+// counter (idx, t, P, cid).  Round 0 and most of round 1 do not depend on the
+// step t, so their results are computed once per slot (pre) and per step
+// (shared by all slots of a lane); philox_step finishes rounds 1..9 and
+// returns the same words as philox4x32_10_rk(idx, t, P, cid).
+struct PhiloxPre {
+    uint32_t c3_1;  // lo(M0 idx) after round 0
+    uint32_t c0_2;  // hi(M1 c2_1) ^ lo(M1 P) ^ rk0[1]
+    uint32_t c1_2;  // lo(M1 c2_1)
+};
+__device__ __forceinline__ PhiloxPre philox_pre(uint32_t idx, uint32_t P, uint32_t cid, const uint32_t (&rk0)[10],
+                                                const uint32_t (&rk1)[10]) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * idx;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * P;
+    const uint32_t c2_1 = (uint32_t)(p0 >> 32) ^ cid ^ rk1[0];
+    const uint32_t c1_1 = (uint32_t)p1;
+    const unsigned long long q1 = (unsigned long long)0xCD9E8D57u * c2_1;
+    PhiloxPre r;
+    r.c3_1 = (uint32_t)p0;
+    r.c0_2 = (uint32_t)(q1 >> 32) ^ c1_1 ^ rk0[1];
+    r.c1_2 = (uint32_t)q1;
+    return r;
+}
+// step part shared by the slots: c0 after round 0 is hi(M1 P) ^ t ^ rk0[0]
+__device__ __forceinline__ unsigned long long philox_step_shared(uint32_t t, uint32_t P, const uint32_t (&rk0)[10]) {
+    const uint32_t c0_1 = (uint32_t)(((unsigned long long)0xCD9E8D57u * P) >> 32) ^ t ^ rk0[0];
+    return (unsigned long long)0xD2511F53u * c0_1;
+}
+__device__ __forceinline__ uint4 philox_step(const PhiloxPre& pre, unsigned long long p0_1, const uint32_t (&rk0)[10],
+                                             const uint32_t (&rk1)[10]) {
+    uint32_t c0 = pre.c0_2, c1 = pre.c1_2;
+    uint32_t c2 = (uint32_t)(p0_1 >> 32) ^ pre.c3_1 ^ rk1[1];
+    uint32_t c3 = (uint32_t)p0_1;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r];
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 // ------------------------------------------------------------ math traits ---
 template <typename T>
 struct Mth;
@@ -444,6 +489,9 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         }
     };
     write_tab();
+    PhiloxPre ppre[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) ppre[b] = philox_pre((uint32_t)(ll + b * W), kPurposeStep, chain_id, c.rk0, c.rk1);
     bool tab_dirty = false;  // anchors moved (flow, recentring) since the table was written
     if (ll == 0) {
         SlotRec<T> zero;
@@ -483,9 +531,10 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         for (int b = 0; b < B; ++b) msk[ll + b * W] = Mask(0);
         // ---- random numbers of this step: block (i, t, STEP, chain) per bead/slot i
         T nrm[B][4], u[B];
+        const unsigned long long p_shared = philox_step_shared(t, kPurposeStep, c.rk0);
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            const uint4 w = philox4x32_10_rk((uint32_t)(ll + b * W), t, kPurposeStep, chain_id, c.rk0, c.rk1);
+            const uint4 w = philox_step(ppre[b], p_shared, c.rk0, c.rk1);
             box_muller<T>(w.x, w.y, nrm[b][0], nrm[b][1]);
             box_muller<T>(w.z, w.w, nrm[b][2], nrm[b][3]);
             u[b] = uniform_lo24<T>(w);
@@ -624,6 +673,17 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         if (Zc >= a.zmax && a.create_mode == 1 && ll == 0 && live) ++cnt_drop;
         const int K = last - first;
         const T pc = c.pc[K];
+        // a slot can change only if it may create (u < 2 p_c on an attempt) or
+        // sits at an end with a destruction hit: the detailed work below runs
+        // only when some slot of the warp can
+        bool cand = WIN;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+            cand |= ((i >= first) && (i < last) && (u[b] < T(2) * pc)) ||
+                    ((i < Zc) && (S[b] == 0 || S[b] == N - 1) && (nrm[b][3] < c.cd));
+        }
+        if (__any_sync(kFull, cand)) {
         int end_new[B];
         bool any_new = false;
 #pragma unroll
@@ -731,6 +791,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             __syncwarp();
             Z = Znew;
         }
+        }  // candidates
 #pragma unroll
         for (int b = 0; b < B; ++b)
 #pragma unroll
@@ -750,12 +811,12 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 const int i = ll + b * W;
                 const Pos<T> p1 = pos[i < N - 1 ? i + 1 : i];
                 const Pos<T> ps = pos[i < Z ? S[b] : 0];
-                T q[3] = {p1.x - R[b][0], p1.y - R[b][1], p1.z - R[b][2]};
-                T dd[3] = {ps.x - A[b][0], ps.y - A[b][1], ps.z - A[b][2]};
-                if (!(i < N - 1)) q[0] = q[1] = q[2] = T(0);
-                if (!(i < Z)) dd[0] = dd[1] = dd[2] = T(0);
+                // the last bead reads itself (q = 0); an empty slot has weight 0
+                const T q[3] = {p1.x - R[b][0], p1.y - R[b][1], p1.z - R[b][2]};
+                const T dd[3] = {ps.x - A[b][0], ps.y - A[b][1], ps.z - A[b][2]};
+                const T ws = i < Z ? c.k_s : T(0);
                 const T kq0 = c.k_b * q[0], kq1 = c.k_b * q[1];
-                const T kd0 = c.k_s * dd[0], kd1 = c.k_s * dd[1];
+                const T kd0 = ws * dd[0], kd1 = ws * dd[1];
                 v[0] += kq0 * q[1];
                 v[1] += kq0 * q[2];
                 v[2] += kq1 * q[2];
