@@ -554,13 +554,9 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             const Pos<T> pl = pos[i > 0 ? i - 1 : 0];
             const Pos<T> pr = pos[i < N - 1 ? i + 1 : i];
             const T Rl[3] = {pl.x, pl.y, pl.z}, Rr[3] = {pr.x, pr.y, pr.z};
+            // an end bead reads itself for its missing neighbour: that term is 0
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                T f = T(0);
-                if (i > 0) f += c.k_b * (Rl[d] - R[b][d]);
-                if (i < N - 1) f += c.k_b * (Rr[d] - R[b][d]);
-                F[b][d] = f;
-            }
+            for (int d = 0; d < 3; ++d) F[b][d] = c.k_b * (Rl[d] - R[b][d]) + c.k_b * (Rr[d] - R[b][d]);
         }
         __syncwarp();
         bool more = false;
@@ -603,17 +599,22 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             }
         }
         T Rn[B][3];
+        if (kap_nz) tab_dirty = true;
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
+            if (kap_nz) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                T flow = T(0);
-                if (kap_nz) flow = kap[3 * d] * R[b][0] + kap[3 * d + 1] * R[b][1] + kap[3 * d + 2] * R[b][2];
-                Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d]) : T(0);
+                for (int d = 0; d < 3; ++d) {
+                    const T flow = kap[3 * d] * R[b][0] + kap[3 * d + 1] * R[b][1] + kap[3 * d + 2] * R[b][2];
+                    Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d]) : T(0);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.amp * nrm[b][d]) : T(0);
             }
             if (kap_nz && i < Z) {
-                tab_dirty = true;
                 T An[3];
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
@@ -642,7 +643,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             if (b * W >= zw) break;
             const int i = ll + b * W;
             const bool occ = i < Z;
-            const int si = occ ? S[b] : 0;
+            const int si = S[b];  // a valid bead index in every slot, occupied or not
             const int sm = si > 0 ? si - 1 : 0;
             const int sp = si < N - 1 ? si + 1 : N - 1;
             const Pos<T> q0 = pos[si], qp = pos[sp], qm = pos[sm];
@@ -948,7 +949,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 // WIN: the differentiation-window hooks (decision tape, snapshots, stress
 // series) are compiled in; the plain kernel carries none of them.
 template <typename T, int W, int B, bool WIN>
-__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_MULTI)
+__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : (B >= 4 ? 4 : SS_CTAS_PER_SM_MULTI))
     chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
     run_chains<T, W, B, WIN>(a, c, blockIdx.x * (kChunkThreads / W), c.NkT, a.t0, a.nsteps, a.log_m0, a.nlog_chunk);
 }
