@@ -256,7 +256,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-ops/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "chunk_kernel<float,16,2>", "kernel_ms": kernel_ms,
+                     "kernel": "chunk_kernel<float, 16, 2, 0>", "kernel_ms": kernel_ms,
                      "kernel_share_of_region": chain_ms / ms_total if ws == 1 else None,
                      "alg_ops_per_bead_step": ALG_OPS_PER_BEAD_STEP,
                      "peak_basis": "152 SMs x 128 lanes x 2070 MHz (nominal max clock), 1 lane-op/lane/clock"},

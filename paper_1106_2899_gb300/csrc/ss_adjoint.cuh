@@ -19,48 +19,80 @@
 namespace ssk {
 
 // ------------------------------------------------- correlator adjoint ------
-// dL/dx(t) and dL/dy(t) of one chain and component from the per-(level, lag)
-// weights wgt[l][k] = dL/d(sum of later x origin products at that lag).
-// Level l pairs block means X_l(m) Y_l(m - k) of 2^l raw samples over complete
-// blocks m < floor(n/2^l); a block mean depends on each of its samples with
-// weight 2^-l.  Block means come from FP64 prefix sums (scratch).
+// dL/dx(t) and dL/dy(t) for every chain and component p = 3 m + c from the
+// per-(level, lag) weights wgt[l][k] = dL/d(sum of later x origin products).
+// Level l pairs block means X_l(j) Y_l(j - k) of 2^l raw samples over complete
+// blocks j < n_l = floor(n / 2^l); a block mean depends on each of its samples
+// with weight 2^-l, so every sample t of block j = t >> l gets
+//   dL/dx += sum_k w_lk Y_l(j - k) / 2^l,   dL/dy += sum_k w_lk X_l(j + k) / 2^l.
+// Three passes, each one thread per (block or sample, p) with p fastest:
+// block means of every level (pairwise, as the forward correlator forms them),
+// the per-block sums cx_l(j), cy_l(j), and the sum over levels per sample.
+// Level arrays are [off_l + j][P] with off_l = sum_{l' < l} n_l'.
+
+// level 0 from the series ([t][M][6]: sigma_off, then (sigma + sigma^(v))_off)
 template <typename T>
-__global__ void corr_adjoint_kernel(const T* __restrict__ series, long long n, int M, int L,
-                                    const double* __restrict__ wgt, double* __restrict__ scratch,
-                                    T* __restrict__ xbar, T* __restrict__ ybar) {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= M * 3) return;
-    const int m = id / 3, cmp = id % 3;
-    double* px = scratch + (size_t)id * 2 * (n + 1);
-    double* py = px + (n + 1);
-    px[0] = py[0] = 0.0;
-    for (long long t = 0; t < n; ++t) {
-        px[t + 1] = px[t] + (double)series[((size_t)t * M + m) * 6 + cmp];
-        py[t + 1] = py[t] + (double)series[((size_t)t * M + m) * 6 + 3 + cmp];
+__global__ void adj_level0_kernel(const T* __restrict__ series, long long n, int M, T* __restrict__ X,
+                                  T* __restrict__ Y) {
+    const long long P = 3ll * M;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * P) return;
+    const long long t = i / P;
+    const int p = (int)(i % P), m = p / 3, c = p % 3;
+    X[i] = series[((size_t)t * M + m) * 6 + c];
+    Y[i] = series[((size_t)t * M + m) * 6 + 3 + c];
+}
+
+// level l from level l - 1: pairwise means
+template <typename T>
+__global__ void adj_level_mean_kernel(T* __restrict__ X, T* __restrict__ Y, long long off_prev, long long off,
+                                      long long nl, long long P) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl * P) return;
+    const long long j = i / P, p = i % P;
+    const long long a = (off_prev + 2 * j) * P + p;
+    X[off * P + i] = T(0.5) * (X[a] + X[a + P]);
+    Y[off * P + i] = T(0.5) * (Y[a] + Y[a + P]);
+}
+
+// cx_l(j), cy_l(j) for one level
+template <typename T>
+__global__ void adj_block_sums_kernel(const T* __restrict__ X, const T* __restrict__ Y, T* __restrict__ CX,
+                                      T* __restrict__ CY, long long off, long long nl, long long P, int l,
+                                      const double* __restrict__ wgt) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl * P) return;
+    const long long j = i / P, p = i % P;
+    const T inv = T(1.0 / (double)(1ll << l));
+    T ax = T(0), ay = T(0);
+    for (int k = (l == 0 ? 0 : kP / 2); k < kP; ++k) {
+        const T w = T(wgt[l * kP + k]);
+        if (w == T(0)) continue;
+        if (j - k >= 0) ax += w * Y[(off + j - k) * P + p];
+        if (j + k < nl) ay += w * X[(off + j + k) * P + p];
     }
-    for (long long t = 0; t < n; ++t) {
-        double xb = 0.0, yb = 0.0;
-        for (int l = 0; l < L; ++l) {
-            const long long Bl = 1ll << l;
-            const long long nl = n >> l, ml = t >> l;
-            if (ml >= nl) break;  // t lies in an incomplete block at this and higher levels
-            const double inv = 1.0 / (double)Bl;
-            for (int k = (l == 0 ? 0 : kP / 2); k < kP; ++k) {
-                const double w = wgt[l * kP + k];
-                if (w == 0.0) continue;
-                if (ml - k >= 0) {
-                    const long long a = (ml - k) * Bl;
-                    xb += w * (py[a + Bl] - py[a]) * inv * inv;
-                }
-                if (ml + k < nl) {
-                    const long long a = (ml + k) * Bl;
-                    yb += w * (px[a + Bl] - px[a]) * inv * inv;
-                }
-            }
-        }
-        xbar[((size_t)t * M + m) * 3 + cmp] = T(xb);
-        ybar[((size_t)t * M + m) * 3 + cmp] = T(yb);
+    CX[off * P + i] = ax * inv;
+    CY[off * P + i] = ay * inv;
+}
+
+// dL/dx(t), dL/dy(t): sum over the levels whose block of t is complete
+template <typename T>
+__global__ void adj_sample_sums_kernel(const T* __restrict__ CX, const T* __restrict__ CY, long long n, long long P,
+                                       int L, T* __restrict__ xbar, T* __restrict__ ybar) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * P) return;
+    const long long t = i / P, p = i % P;
+    T xb = T(0), yb = T(0);
+    long long off = 0;
+    for (int l = 0; l < L; ++l) {
+        const long long nl = n >> l, j = t >> l;
+        if (j >= nl) break;
+        xb += CX[(off + j) * P + p];
+        yb += CY[(off + j) * P + p];
+        off += nl;
     }
+    xbar[i] = xb;  // [t][M][3]
+    ybar[i] = yb;
 }
 
 // ------------------------------------------------------- reverse sweep -----
@@ -121,9 +153,13 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
             Rb[b][d] = live ? gRb[((size_t)mm * 3 + d) * NP + ll + b * W] : T(0);
             Ab[b][d] = live ? gAb[((size_t)mm * 3 + d) * NP + ll + b * W] : T(0);
         }
+    // gradient sums: per-step parts in T, folded into FP64 every 32 steps
     double gkb = 0.0, gks = 0.0, gz = 0.0;
+    T tkb = T(0), tks = T(0), tz = T(0);
     const T mu = c.mob, kb = c.k_b, ks = c.k_s;
     const double zeta = (double)c.dt / (double)c.mob;
+    const double inv_zeta = 1.0 / zeta;
+    const T half_amp = T(0.5) * c.amp;
 
     // per-bead slot masks of a state (springs grouped by bead, in slot order)
     auto build_masks = [&](const int (&Sx)[B], int Zx) {
@@ -138,6 +174,9 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
         __syncwarp();
     };
 
+    PhiloxPre ppre[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) ppre[b] = philox_pre((uint32_t)(ll + b * W), kPurposeStep, chain_id, c.rk0, c.rk1);
     for (int t = a.ns - 1; t >= 0; --t) {
         // ------------------------------------------ state after the step
         T Ra[B][3], Aa[B][3];
@@ -187,7 +226,7 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
                 v.z = kb * (g[1] * q[0] + g[2] * q[1]);
                 v.w = T(0);
                 vec[i] = v;
-                gkb += (double)(g[0] * q[0] * q[1] + g[1] * q[0] * q[2] + g[2] * q[1] * q[2]);
+                tkb += g[0] * q[0] * q[1] + g[1] * q[0] * q[2] + g[2] * q[1] * q[2];
             }
             __syncwarp();
 #pragma unroll
@@ -226,7 +265,7 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
                 r.z = wz;
                 r.s = 0;
                 tab[i] = r;
-                gks += (double)(h[0] * dd[0] * dd[1] + h[1] * dd[0] * dd[2] + h[2] * dd[1] * dd[2]);
+                tks += h[0] * dd[0] * dd[1] + h[1] * dd[0] * dd[2] + h[2] * dd[1] * dd[2];
             }
             __syncwarp();
 #pragma unroll
@@ -415,27 +454,29 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
                     asum[2] += r.z;
                 }
                 // noise of this bead in this step
-                const uint4 w = philox4x32_10_rk((uint32_t)i, tt, kPurposeStep, chain_id, c.rk0, c.rk1);
+                const uint4 w = philox_step(ppre[b], philox_step_shared(tt, kPurposeStep, c.rk0), c.rk0, c.rk1);
                 T nrm[4];
                 box_muller<T>(w.x, w.y, nrm[0], nrm[1]);
                 box_muller<T>(w.z, w.w, nrm[2], nrm[3]);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    T fb = T(0), lap = T(0);
+                    T fbk = T(0), lap = T(0);  // bond force / k_b, Laplacian of the adjoint
                     if (i > 0) {
-                        fb += kb * (xl[d] - R0[b][d]);
+                        fbk += xl[d] - R0[b][d];
                         lap += bl[d] - rb[d];
                     }
                     if (i < N - 1) {
-                        fb += kb * (xr[d] - R0[b][d]);
+                        fbk += xr[d] - R0[b][d];
                         lap += br[d] - rb[d];
                     }
+                    const T fb = kb * fbk;
                     const T fs = ks * (asum[d] - nsp * R0[b][d]);
                     Rn[b][d] = bead ? rb[d] + mu * (kb * lap - ks * nsp * rb[d]) : T(0);
                     if (bead) {
-                        gkb += (double)mu * (double)rb[d] * (double)fb / (double)kb;
-                        gz += (double)rb[d] * (-(double)mu * (double)(fb + fs) / zeta -
-                                               (double)c.amp * (double)nrm[d] / (2.0 * zeta));
+                        // d/dk_b of mu F_b is mu F_b / k_b; d/dzeta of the update is
+                        // -(mu F + amp w / 2) / zeta
+                        tkb += mu * rb[d] * fbk;
+                        tz += rb[d] * (mu * (fb + fs) + half_amp * nrm[d]);
                     }
                 }
             }
@@ -449,9 +490,7 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
                     Ab[b][0] += mu * ks * vs.x;
                     Ab[b][1] += mu * ks * vs.y;
                     Ab[b][2] += mu * ks * vs.z;
-                    gks += (double)mu * ((double)vs.x * (double)(A0[b][0] - ps.x) +
-                                         (double)vs.y * (double)(A0[b][1] - ps.y) +
-                                         (double)vs.z * (double)(A0[b][2] - ps.z));
+                    tks += mu * (vs.x * (A0[b][0] - ps.x) + vs.y * (A0[b][1] - ps.y) + vs.z * (A0[b][2] - ps.z));
                 } else {
                     Ab[b][0] = Ab[b][1] = Ab[b][2] = T(0);
                 }
@@ -461,6 +500,12 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
 #pragma unroll
                 for (int d = 0; d < 3; ++d) Rb[b][d] = Rn[b][d];
             __syncwarp();
+        }
+        if ((t & 31) == 0) {
+            gkb += (double)tkb;
+            gks += (double)tks;
+            gz -= (double)tz * inv_zeta;
+            tkb = tks = tz = T(0);
         }
     }
     // ---- carry the adjoints to the previous segment, add this chain's gradient

@@ -949,10 +949,34 @@ int window_backward_t(ss_ctx* c, const double* dL_dG, double grad[3]) {
         }
     SS_CUDA(c, cudaMemcpyAsync(w.wgt, wg.data(), sizeof(double) * wg.size(), cudaMemcpyHostToDevice, c->stream));
     {
-        const int thr = 128, n = e.M * 3;
-        ssk::corr_adjoint_kernel<T><<<(n + thr - 1) / thr, thr, 0, c->stream>>>(
-            static_cast<const T*>(w.series), w.n, e.M, L, w.wgt, w.scratch, static_cast<T*>(w.xbar),
-            static_cast<T*>(w.ybar));
+        // correlator adjoint: block means per level, per-block lag sums, per-sample sums
+        const long long P = 3ll * e.M, n = w.n, cap = 2 * (n + 1) * P;
+        T* X = reinterpret_cast<T*>(w.scratch);
+        T* Y = X + cap;
+        T* CX = Y + cap;
+        T* CY = CX + cap;
+        const int thr = 256;
+        auto blocks = [&](long long items) { return (unsigned)((items + thr - 1) / thr); };
+        ssk::adj_level0_kernel<T><<<blocks(n * P), thr, 0, c->stream>>>(static_cast<const T*>(w.series), n, e.M, X, Y);
+        SS_CUDA(c, cudaGetLastError());
+        c->launches++;
+        long long off = 0;
+        for (int l = 0; l < L && (n >> l) > 0; ++l) {
+            const long long nl = n >> l;
+            if (l > 0) {
+                ssk::adj_level_mean_kernel<T><<<blocks(nl * P), thr, 0, c->stream>>>(X, Y, off - (n >> (l - 1)), off,
+                                                                                   nl, P);
+                SS_CUDA(c, cudaGetLastError());
+                c->launches++;
+            }
+            ssk::adj_block_sums_kernel<T><<<blocks(nl * P), thr, 0, c->stream>>>(X, Y, CX, CY, off, nl, P, l, w.wgt);
+            SS_CUDA(c, cudaGetLastError());
+            c->launches++;
+            off += nl;
+        }
+        ssk::adj_sample_sums_kernel<T><<<blocks(n * P), thr, 0, c->stream>>>(CX, CY, n, P, L,
+                                                                             static_cast<T*>(w.xbar),
+                                                                             static_cast<T*>(w.ybar));
         SS_CUDA(c, cudaGetLastError());
         c->launches++;
     }
@@ -1494,7 +1518,7 @@ int ss_window_forward(ss_ctx* c, int64_t n_steps, int checkpoint_every, int repl
         SS_CUDA(c, cudaMalloc(&w.snZ, (size_t)(w.ce + 1) * e.M * sizeof(int32_t)));
         SS_CUDA(c, cudaMalloc(&w.xbar, (size_t)n_steps * e.M * 3 * ts));
         SS_CUDA(c, cudaMalloc(&w.ybar, (size_t)n_steps * e.M * 3 * ts));
-        SS_CUDA(c, cudaMalloc(&w.scratch, (size_t)e.M * 3 * 2 * (n_steps + 1) * sizeof(double)));
+        SS_CUDA(c, cudaMalloc(&w.scratch, (size_t)8 * (n_steps + 1) * e.M * 3 * ts));  // 4 level arrays of 2(n+1) rows
         SS_CUDA(c, cudaMalloc(&w.Rb, stR));
         SS_CUDA(c, cudaMalloc(&w.Ab, stR));
         SS_CUDA(c, cudaMalloc(&w.grad, (size_t)e.M * 3 * sizeof(double)));

@@ -30,6 +30,7 @@ constexpr uint32_t kPurposeStep = 1, kPurposeCreate = 2, kPurposeInitBond = 3,
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBeads = 64;
 constexpr int kSliceChains = 64;  // chains per FP64 correlator/log slice
+constexpr int kMaxCorrLevels = 32;  // correlator levels the library accepts
 
 // ---------------------------------------------------------------- Philox ----
 // Ten rounds of the Philox4x32 bijection: words 0 and 2 are multiplied by

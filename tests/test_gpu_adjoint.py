@@ -14,6 +14,8 @@ decision frozen.  It is checked
 
 A replay at the base parameters must reproduce the recorded window bit for bit.
 """
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -244,9 +246,17 @@ def test_fp32_full_window_against_finite_differences_and_oracle_target():
     start = g.get_state()
     fit = GFit(g, start, n_steps=n, checkpoint_every=ce, target=target)
     theta = torch.tensor(THETA0, dtype=torch.float64, requires_grad=True)
+    g.synchronize()
+    t_a = time.perf_counter()
     loss = fit(theta)
+    g.synchronize()
+    t_b = time.perf_counter()
     loss.backward()
+    g.synchronize()
+    t_c = time.perf_counter()
     adj = theta.grad.numpy().copy()
+    print("\nwindow of %d chains x N=%d x %d steps: forward %.3g bead-steps/s, backward %.3g bead-steps/s"
+          % (M, N, n, M * N * n / (t_b - t_a), M * N * n / (t_c - t_b)))
     assert fit.mask.sum() >= 20
     fd = _fd(fit, THETA0)
     print("\nadjoint %s\nFD      %s\nloss %.6g over %d slots" % (adj, fd, loss.item(), fit.mask.sum()))
