@@ -194,6 +194,9 @@ def run_ours(args):
     achieved = alg_ops_launch / (kernel_ms / 1e3)
     peak = SMS * LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6
     status = g.status()
+    tg, Gg, sg = g.correlator("total")
+    dt_step = synth.PAPER["dt"]
+    gpu_G = {int(round(tt / dt_step)): (float(a), float(b)) for tt, a, b in zip(tg, Gg, sg)}
     g.close()
 
     # ---------------- plain one-step-per-launch form (same library, chunk = 1)
@@ -250,7 +253,7 @@ def run_ours(args):
         "config": {"workload": "lve: %d chains x N=32, FP32 beads / FP64 sums, multiple-tau 16x24, "
                                "paper parameters N0=4 Ns=0.5 zeta_s=0.1 dt=0.01" % M,
                    "chains": M, "beads": N, "steps_per_call": spc, "steps_per_launch": args.chunk,
-                   "l2": "working set (state + correlator, ~1.2 GB) larger than L2",
+                   "l2": "working set (state, stress series, correlator buffers, ~3.9 GB) larger than L2",
                    "parallelism": "independent chains; ranks run disjoint chains" if ws > 1 else "1 GPU"},
         "plain": {"value": plain_value, "unit": "bead-steps/s", "steps": args.plain_steps,
                   "form": "one step per launch, state and correlator through HBM, FP64 flush every step",
@@ -270,7 +273,9 @@ def run_ours(args):
         "hbm_peak_measured_gbs": pk.get("hbm_gbs"),
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_chains, args.cpu_steps)
+        cb = cpu_baseline(args.cpu_chains, args.cpu_steps)
+        out["g_err_vs_oracle"] = g_error(gpu_G, cb.pop("_G"))
+        out["cpu_baseline"] = cb
     return out
 
 
@@ -286,9 +291,42 @@ def cpu_baseline(M=4096, steps=3000, nthreads=0):
     t = time.perf_counter()
     e.run(steps, nthreads=nthreads)
     dt = time.perf_counter() - t
+    # G(t) of the TOTAL channel per multiple-tau slot, mean and SE over the 32 groups
+    acc, n = e.corr_sums()
+    cnt = oracle.corr_counts(n, w["levels"])
+    lags = oracle.corr_lags(w["levels"])
+    per_group = np.array([(g + 1) * M // 32 - g * M // 32 for g in range(32)], dtype=float)
+    G = {}
+    for l in range(w["levels"]):
+        for k in range(16):
+            if lags[l, k] < 0 or cnt[l, k] <= 0:
+                continue
+            gk = acc[:, l, k, 1, :].sum(axis=-1) / 3.0 / (cnt[l, k] * per_group * w["N"] * p.kT * p.kT)
+            G[int(lags[l, k])] = (float(gk.mean()), float(gk.std(ddof=1) / np.sqrt(len(gk))))
     return {"value": M * w["N"] * steps / dt, "unit": "bead-steps/s", "cores": nthreads, "kind": "oracle",
             "sample": "%d chains x N=%d x %d steps of the lve workload (correlator 16x24), %.1f s" % (
-                M, w["N"], steps, dt)}
+                M, w["N"], steps, dt), "_G": G}
+
+
+def g_error(gpu, ora, max_lag=2000):
+    """G(t) of the benchmark run against the oracle's independent FP64 ensemble at
+    common lags up to max_lag steps: z-scores |dG| / sqrt(SE_gpu^2 + SE_oracle^2), and
+    the relative error where the oracle resolves G to 0.5%."""
+    zs, rel = [], []
+    for lag, (gg, sg) in gpu.items():
+        if lag > max_lag or lag not in ora:
+            continue
+        go, so = ora[lag]
+        zs.append(abs(gg - go) / np.sqrt(sg * sg + so * so))
+        if so < 0.005 * abs(go):
+            rel.append(abs(gg - go) / abs(go))
+    if not zs:
+        return None
+    zs = np.array(zs)
+    return {"channel": "TOTAL", "lags_compared": int(len(zs)), "max_lag_steps": max_lag,
+            "max_z": float(zs.max()), "frac_z_below_3": float(np.mean(zs < 3.0)),
+            "max_rel_err_where_resolved": float(max(rel)) if rel else None, "resolved_lags": len(rel),
+            "oracle": "independent FP64 ensemble of the cpu_baseline leg (other chains)"}
 
 
 def run_reference(args):
@@ -299,6 +337,7 @@ def run_reference(args):
     cb = None
     for k in range(args.warmup + args.steps):
         cb = cpu_baseline(args.cpu_chains, max(50, args.cpu_steps // 5))
+        cb.pop("_G")
         if k >= args.warmup:
             vals.append(cb["value"])
     value = float(np.mean(vals))

@@ -96,7 +96,10 @@ typedef struct {
     int32_t corr_levels;    /* multiple-tau levels, 1..SS_MAX_LEVELS [24]; < 0: none      */
     int32_t groups;         /* chain groups per element for standard errors [32]         */
     int32_t chunk_steps;    /* steps per kernel launch [1024]; 1 gives the plain
-                               one-step-per-launch form                                  */
+                               one-step-per-launch form.  With the correlator on, a
+                               launch covers at most 1024 steps (larger values are
+                               reduced to 1024): the launch's stress series, 24 B per
+                               chain and step in FP32, is what the correlator reads */
 } ss_params;
 
 /* Create a context for n_elems elements.  precision: SS_FP32 or SS_FP64.
