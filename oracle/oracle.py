@@ -75,6 +75,10 @@ def _load():
     lib.or_ens_run_tape.restype = C.c_int
     lib.or_ens_set_step.argtypes = [C.c_void_p, C.c_int64]
     lib.or_ens_set_step.restype = None
+    lib.or_corr_series_tt.argtypes = [dp, C.c_int64, C.c_int, dp, dp]
+    lib.or_corr_series_tt.restype = None
+    lib.or_ens_corr_tt.argtypes = [C.c_void_p, dp]
+    lib.or_ens_corr_tt.restype = None
     _lib = lib
     return lib
 
@@ -287,6 +291,13 @@ class Ensemble:
         self.lib.or_ens_corr(self.h, _ptr(acc, C.c_double), C.byref(n))
         return acc, n.value
 
+    def corr_sums_tt(self):
+        """Group sums [G][levels][P][3] of channel TT (later sigma + sigma_v times
+        origin sigma + sigma_v)."""
+        acc = np.zeros((self.G, self.levels, CORR_P, 3))
+        self.lib.or_ens_corr_tt(self.h, _ptr(acc, C.c_double))
+        return acc
+
     def logs(self):
         """(log_step [n], sums [n][G][14]) — sums of sigma xx,yy,zz,xy,xz,yz,
         their squares, Z and Z^2 over each group's chains."""
@@ -305,12 +316,18 @@ class Ensemble:
         return dict(zip(["hops_up", "hops_down", "created", "destroyed", "dropped"], out.tolist()))
 
 
-def corr_series(x, levels: int):
-    """Streaming multiple-tau sums [levels][P][2][3] of one series x[T][6]."""
+def corr_series(x, levels: int, tt: bool = False):
+    """Streaming multiple-tau sums [levels][P][2][3] of one series x[T][6]; with
+    tt also the channel-TT sums [levels][P][3]."""
     xx = np.ascontiguousarray(x, dtype=np.float64)
     acc = np.zeros((levels, CORR_P, 2, 3))
-    _load().or_corr_series(_ptr(xx, C.c_double), xx.shape[0], levels, _ptr(acc, C.c_double))
-    return acc
+    if not tt:
+        _load().or_corr_series(_ptr(xx, C.c_double), xx.shape[0], levels, _ptr(acc, C.c_double))
+        return acc
+    acc_tt = np.zeros((levels, CORR_P, 3))
+    _load().or_corr_series_tt(_ptr(xx, C.c_double), xx.shape[0], levels, _ptr(acc, C.c_double),
+                              _ptr(acc_tt, C.c_double))
+    return acc, acc_tt
 
 
 def corr_counts(n_samples: int, levels: int, P: int = CORR_P):

@@ -397,7 +397,10 @@ void or_stress(const or_params* p, const or_chain* c, double sig[9], double sigv
  * lags k*2^l for k = OR_P/2 .. OR_P-1.  Each sample x holds six signals:
  * sigma_xy, sigma_xz, sigma_yz and the same components of sigma + sigma_v.
  * Channel 0 accumulates later sigma times origin sigma (AUTO); channel 1 later
- * sigma times origin sigma + sigma_v (TOTAL). */
+ * sigma times origin sigma + sigma_v (TOTAL); the optional channel TT (acc_tt)
+ * later sigma + sigma_v times origin sigma + sigma_v, whose difference with
+ * TOTAL is the virtual-stress numerator of Sec. 4.2 (Eq.
+ * relative_contribution_virtual_stress_to_shear_relaxation_modulus). */
 typedef struct {
     double hist[OR_LMAX][OR_P][6];
     int64_t nfill[OR_LMAX];
@@ -405,8 +408,8 @@ typedef struct {
     int npend[OR_LMAX];
 } or_corr_chain;
 
-static void or_corr_push(or_corr_chain* cc, double* acc /* [levels][P][2][3] */, int levels, int l,
-                         const double v[6]) {
+static void or_corr_push(or_corr_chain* cc, double* acc /* [levels][P][2][3] */,
+                         double* acc_tt /* [levels][P][3] or NULL */, int levels, int l, const double v[6]) {
     for (int k = OR_P - 1; k > 0; --k) memcpy(cc->hist[l][k], cc->hist[l][k - 1], sizeof(double) * 6);
     memcpy(cc->hist[l][0], v, sizeof(double) * 6);
     cc->nfill[l]++;
@@ -418,6 +421,10 @@ static void or_corr_push(or_corr_chain* cc, double* acc /* [levels][P][2][3] */,
             a[c] += v[c] * cc->hist[l][k][c];
             a[3 + c] += v[c] * cc->hist[l][k][3 + c];
         }
+        if (acc_tt) {
+            double* b = acc_tt + ((size_t)l * OR_P + (size_t)k) * 3;
+            for (int c = 0; c < 3; ++c) b[c] += v[3 + c] * cc->hist[l][k][3 + c];
+        }
     }
     for (int s = 0; s < 6; ++s) cc->pend[l][s] += v[s];
     cc->npend[l]++;
@@ -426,13 +433,17 @@ static void or_corr_push(or_corr_chain* cc, double* acc /* [levels][P][2][3] */,
         for (int s = 0; s < 6; ++s) up[s] = 0.5 * cc->pend[l][s];
         memset(cc->pend[l], 0, sizeof(cc->pend[l]));
         cc->npend[l] = 0;
-        if (l + 1 < levels) or_corr_push(cc, acc, levels, l + 1, up);
+        if (l + 1 < levels) or_corr_push(cc, acc, acc_tt, levels, l + 1, up);
     }
 }
 
 void or_corr_series(const double* x, int64_t T, int levels, double* acc) {
+    or_corr_series_tt(x, T, levels, acc, NULL);
+}
+
+void or_corr_series_tt(const double* x, int64_t T, int levels, double* acc, double* acc_tt) {
     or_corr_chain* cc = (or_corr_chain*)calloc(1, sizeof(or_corr_chain));
-    for (int64_t t = 0; t < T; ++t) or_corr_push(cc, acc, levels, 0, x + 6 * t);
+    for (int64_t t = 0; t < T; ++t) or_corr_push(cc, acc, acc_tt, levels, 0, x + 6 * t);
     free(cc);
 }
 
@@ -452,6 +463,7 @@ struct or_ens {
     or_chain* ch;
     or_corr_chain* cc;
     double* acc;  /* [G][levels][P][6] */
+    double* acc_tt; /* [G][levels][P][3] */
     double* logs; /* [max_logs][G][14] */
     int64_t* log_step;
     int64_t n_samples;
@@ -480,6 +492,7 @@ or_ens* or_ens_create(const or_params* p, uint64_t seed, int M, uint32_t chain_o
     e->ch = (or_chain*)calloc((size_t)M, sizeof(or_chain));
     e->cc = (or_corr_chain*)calloc((size_t)M, sizeof(or_corr_chain));
     e->acc = (double*)calloc((size_t)G * levels * OR_P * 6, sizeof(double));
+    e->acc_tt = (double*)calloc((size_t)G * levels * OR_P * 3, sizeof(double));
     e->logs = (double*)calloc((size_t)(e->max_logs ? e->max_logs : 1) * G * 14, sizeof(double));
     e->log_step = (int64_t*)calloc((size_t)(e->max_logs ? e->max_logs : 1), sizeof(int64_t));
     e->capflow = 16;
@@ -493,6 +506,7 @@ void or_ens_destroy(or_ens* e) {
     free(e->ch);
     free(e->cc);
     free(e->acc);
+    free(e->acc_tt);
     free(e->logs);
     free(e->log_step);
     free(e->flow);
@@ -569,7 +583,7 @@ int or_ens_run_tape(or_ens* e, int64_t n_steps, int nthreads, int32_t* Z_tr, int
                 double sig[9], sigv[9];
                 or_stress(&e->p, c, sig, sigv);
                 double v[6] = {sig[1], sig[2], sig[5], sig[1] + sigv[1], sig[2] + sigv[2], sig[5] + sigv[5]};
-                or_corr_push(cc, acc, e->levels, 0, v);
+                or_corr_push(cc, acc, e->acc_tt + (size_t)g * e->levels * OR_P * 3, e->levels, 0, v);
                 if (e->log_every > 0 && (t + 1) % e->log_every == 0) {
                     double* L = e->logs + ((size_t)lg * G + (size_t)g) * 14;
                     double comp[6] = {sig[0], sig[4], sig[8], sig[1], sig[2], sig[5]};
@@ -633,6 +647,10 @@ void or_ens_corr(const or_ens* e, double* acc, int64_t* n_samples) {
     if (n_samples) *n_samples = e->n_samples;
 }
 
+void or_ens_corr_tt(const or_ens* e, double* acc_tt) {
+    memcpy(acc_tt, e->acc_tt, sizeof(double) * (size_t)e->G * e->levels * OR_P * 3);
+}
+
 int or_ens_logs(const or_ens* e, double* logs, int64_t* log_step, int cap) {
     int n = e->nlogs < cap ? e->nlogs : cap;
     if (logs) memcpy(logs, e->logs, sizeof(double) * (size_t)n * e->G * 14);
@@ -643,6 +661,7 @@ int or_ens_logs(const or_ens* e, double* logs, int64_t* log_step, int cap) {
 void or_ens_reset_obs(or_ens* e) {
     memset(e->cc, 0, sizeof(or_corr_chain) * (size_t)e->M);
     memset(e->acc, 0, sizeof(double) * (size_t)e->G * e->levels * OR_P * 6);
+    memset(e->acc_tt, 0, sizeof(double) * (size_t)e->G * e->levels * OR_P * 3);
     memset(e->logs, 0, sizeof(double) * (size_t)(e->max_logs ? e->max_logs : 1) * e->G * 14);
     e->nlogs = 0;
     e->n_samples = 0;

@@ -122,6 +122,9 @@ double or_norm_ppf(double p);
  * sigma + sigma_v); adds into acc[levels][OR_P][2][3].  Pinned against the
  * batch definition (block means, lag products). */
 void or_corr_series(const double* x, int64_t T, int levels, double* acc);
+/* The same, also accumulating channel TT (later sigma + sigma_v times origin
+ * sigma + sigma_v) into acc_tt[levels][OR_P][3] when acc_tt is not NULL. */
+void or_corr_series_tt(const double* x, int64_t T, int levels, double* acc, double* acc_tt);
 
 /* ---- ensemble runner (mirrors the library's calls) ----------------------- */
 typedef struct or_ens or_ens;
@@ -152,6 +155,8 @@ void or_ens_set_step(or_ens* e, int64_t step);
 /* correlator group sums acc[G][levels][OR_P][2 channels][3 comps] and the
  * number of samples pushed so far (per chain) */
 void or_ens_corr(const or_ens* e, double* acc, int64_t* n_samples);
+/* group sums of channel TT, acc_tt[G][levels][OR_P][3 comps] */
+void or_ens_corr_tt(const or_ens* e, double* acc_tt);
 /* logs[n][G][14]: sums of sigma (xx,yy,zz,xy,xz,yz), sigma^2 (same order), Z, Z^2;
  * log_step[n] = step index after which log n was taken.  Returns n. */
 int or_ens_logs(const or_ens* e, double* logs, int64_t* log_step, int cap);

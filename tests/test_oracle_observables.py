@@ -56,6 +56,21 @@ def test_multitau_streaming_equals_batch_definition(T):
     assert np.allclose(ones[:, :, 0, 0], cnt)
 
 
+@pytest.mark.parametrize("T", [33, 1000])
+def test_multitau_tt_channel_equals_batch_definition(T):
+    """Channel TT (later and origin both sigma + sigma_v, the numerator of the
+    virtual-stress share of Sec. 4.2 minus TOTAL): the batch definition applied
+    to the series whose sigma columns are the sigma + sigma_v columns."""
+    rng = np.random.default_rng(T + 7)
+    x = rng.normal(size=(T, 6)) + 0.2
+    levels = 9
+    acc, acc_tt = oracle.corr_series(x, levels, tt=True)
+    assert np.allclose(acc, oracle.corr_series(x, levels), rtol=0, atol=0)
+    swapped = np.concatenate([x[:, 3:6], x[:, 3:6]], axis=1)
+    want = _batch_multitau(swapped, levels)[:, :, 0, :]
+    assert np.allclose(acc_tt, want, rtol=1e-12, atol=1e-9)
+
+
 # -------------------------------------------------------------- Rouse -------
 def _rouse_exact(N, k_b, dt, zeta, kT, levels):
     L = np.zeros((N, N))
