@@ -56,6 +56,10 @@ extern "C" {
 #define SS_CH_AUTO 0  /* (1/N) <sigma_ab(t) sigma_ab(0)>                 */
 #define SS_CH_CROSS 1 /* (1/N) <sigma_ab(t) sigma^(v)_ab(0)>             */
 #define SS_CH_TOTAL 2 /* AUTO + CROSS: the paper's G(t)                   */
+/* with corr_tt = 1 (Sec. 4.2, Eq. relative_contribution_virtual_stress_to_
+ * shear_relaxation_modulus: the virtual-stress share is VIRTUAL / TOTAL) */
+#define SS_CH_TT 3      /* (1/N) <(sigma + sigma^(v))_ab(t) (sigma + sigma^(v))_ab(0)> */
+#define SS_CH_VIRTUAL 4 /* TT - TOTAL = (1/N) <sigma^(v)_ab(t) (sigma + sigma^(v))_ab(0)> */
 
 #define SS_CORR_POINTS 16 /* multiple-tau points per level */
 #define SS_MAX_LEVELS 32
@@ -100,6 +104,8 @@ typedef struct {
                                launch covers at most 1024 steps (larger values are
                                reduced to 1024): the launch's stress series, 24 B per
                                chain and step in FP32, is what the correlator reads */
+    int32_t corr_tt;        /* 1: also correlate sigma + sigma^(v) with itself (channels
+                               SS_CH_TT, SS_CH_VIRTUAL) [0]                             */
 } ss_params;
 
 /* Create a context for n_elems elements.  precision: SS_FP32 or SS_FP64.
@@ -206,6 +212,9 @@ int ss_reset_observables(ss_ctx* ctx);
  * n_groups groups; *n_samples = samples per chain since the last reset.
  * Level l >= 1 only fills lag slots 8..15 (lag slot k means k 2^l steps). */
 int ss_corr_sums(ss_ctx* ctx, int elem, double* acc, int* n_groups, int64_t* n_samples);
+/* Group sums of channel TT, acc_tt[n_groups][levels][16][3] (lag-major as in
+ * ss_corr_sums, one channel).  SS_ESTATE unless corr_tt = 1. */
+int ss_corr_sums_tt(ss_ctx* ctx, int elem, double* acc_tt, int* n_groups, int64_t* n_samples);
 
 /* Raw stress-log sums of element elem: sums[n][g][14] = sums over group g of
  * sigma xx,yy,zz,xy,xz,yz, their squares, Z and Z^2; log_step[n] = steps done

@@ -13,7 +13,7 @@ ERRORS = {-1: "SS_EINVAL", -2: "SS_ENOMEM", -3: "SS_ECUDA", -4: "SS_EOVERFLOW", 
           -6: "SS_ETIMEOUT", -7: "SS_ETOOBIG"}
 SS_NOALLOC_SCRATCH_BYTES = 32 << 20
 SS_FP32, SS_FP64 = 0, 1
-SS_CH_AUTO, SS_CH_CROSS, SS_CH_TOTAL = 0, 1, 2
+SS_CH_AUTO, SS_CH_CROSS, SS_CH_TOTAL, SS_CH_TT, SS_CH_VIRTUAL = 0, 1, 2, 3, 4
 
 # every symbol include/slipspring.h declares
 EXPORTS = ["ss_create", "ss_set_params", "ss_set_flow", "ss_run", "ss_stress", "ss_correlator",
@@ -21,7 +21,7 @@ EXPORTS = ["ss_create", "ss_set_params", "ss_set_flow", "ss_run", "ss_stress", "
            "ss_reset_observables", "ss_corr_sums", "ss_log_sums", "ss_counters", "ss_status",
            "ss_synchronize", "ss_run_noalloc", "ss_kernel_timing", "ss_kernel_time",
            "ss_set_chain_offset", "ss_set_flow_table", "ss_set_batched", "ss_window_forward",
-           "ss_window_backward", "ss_set_coefficients", "ss_set_step_count"]
+           "ss_window_backward", "ss_set_coefficients", "ss_set_step_count", "ss_corr_sums_tt"]
 
 
 class ss_element(C.Structure):
@@ -34,7 +34,7 @@ class ss_params(C.Structure):
                 ("k_s", C.c_double), ("create_mode", C.c_int32), ("z_max", C.c_int32),
                 ("destroy_new", C.c_int32), ("recenter_every", C.c_int32), ("log_every", C.c_int32),
                 ("max_logs", C.c_int32), ("corr_levels", C.c_int32), ("groups", C.c_int32),
-                ("chunk_steps", C.c_int32)]
+                ("chunk_steps", C.c_int32), ("corr_tt", C.c_int32)]
 
 
 class SlipSpringError(RuntimeError):
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
         "ss_window_backward": [vp, dp, dp],
         "ss_set_coefficients": [vp, C.c_double, C.c_double, C.c_double],
         "ss_set_step_count": [vp, C.c_int64],
+        "ss_corr_sums_tt": [vp, C.c_int, dp, P(C.c_int), i64p],
         "ss_kernel_time": [vp, dp, i64p],
         "ss_run_noalloc": [P(ss_params), C.c_int, C.c_uint64, C.c_int32, C.c_int32, C.c_uint32, C.c_int64,
                            C.c_int64, dp, vp, vp, vp, vp, vp, vp, vp],

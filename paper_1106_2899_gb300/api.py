@@ -14,7 +14,8 @@ import numpy as np
 
 from . import _native as nat
 
-CHANNELS = {"auto": nat.SS_CH_AUTO, "cross": nat.SS_CH_CROSS, "total": nat.SS_CH_TOTAL}
+CHANNELS = {"auto": nat.SS_CH_AUTO, "cross": nat.SS_CH_CROSS, "total": nat.SS_CH_TOTAL, "tt": nat.SS_CH_TT,
+            "virtual": nat.SS_CH_VIRTUAL}
 
 
 def _p(a, ctype):
@@ -181,6 +182,17 @@ class SlipSpring:
         acc = np.zeros((g.value, levels, 16, 2, 3))
         self._chk(self.lib.ss_corr_sums(self.h, elem, _p(acc, C.c_double), C.byref(g), C.byref(n)),
                   "ss_corr_sums")
+        return acc, n.value
+
+    def corr_sums_tt(self, elem=0):
+        """(acc [G][levels][16][3], n_samples) group sums of channel TT (corr_tt=1)."""
+        levels = (self.params or {}).get("corr_levels", 0) or 24
+        g = C.c_int()
+        n = C.c_int64()
+        self._chk(self.lib.ss_corr_sums_tt(self.h, elem, None, C.byref(g), C.byref(n)), "ss_corr_sums_tt")
+        acc = np.zeros((g.value, levels, 16, 3))
+        self._chk(self.lib.ss_corr_sums_tt(self.h, elem, _p(acc, C.c_double), C.byref(g), C.byref(n)),
+                  "ss_corr_sums_tt")
         return acc, n.value
 
     def log_sums(self, elem=0):

@@ -35,6 +35,7 @@ struct Elem {
     int32_t* Z = nullptr;
     void* hist = nullptr;    // [M][L][6][16] T: newest 16 samples per correlator level and series row
     double* acc64 = nullptr;  // [slices][L][96] FP64 sums
+    double* acc64tt = nullptr;  // [slices][L][48] FP64 sums of channel TT (optional)
     void* ser = nullptr;     // [ser_cap][M][6] T: stress series of one launch
     void* lev = nullptr;     // [2][ser_cap / 2 + 1][M][6] T: correlator level samples (ping-pong)
     int ser_cap = 0;
@@ -135,13 +136,13 @@ int fail(ss_ctx* c, int code, const std::string& msg) {
 size_t tsize(const ss_ctx* c) { return c->prec == SS_FP64 ? sizeof(double) : sizeof(float); }
 
 void free_elem(Elem& e) {
-    void* ptrs[] = {e.R, e.A, e.S, e.Z, e.hist, e.acc64, e.ser, e.lev, e.logs, e.kap_d, e.kfrom_d};
+    void* ptrs[] = {e.R, e.A, e.S, e.Z, e.hist, e.acc64, e.acc64tt, e.ser, e.lev, e.logs, e.kap_d, e.kfrom_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     e.R = e.A = e.hist = e.ser = e.lev = nullptr;
     e.ser_cap = 0;
     e.S = e.Z = nullptr;
-    e.acc64 = e.logs = e.kap_d = nullptr;
+    e.acc64 = e.acc64tt = e.logs = e.kap_d = nullptr;
     e.kfrom_d = nullptr;
     e.n_kap_d = 0;
 }
@@ -223,14 +224,14 @@ ssk::StepConst<T> step_const(const ss_ctx* c, int N) {
 // CTA folds its slice's sums into acc64.  n0: samples before the launch; lev:
 // two level-sample buffers of lev_half elements.  Returns the number of
 // kernels launched, or -1.
-template <typename T>
-int corr_launches(const T* ser, int ns, int M, int L, long long n0, T* hist, double* acc64, T* lev,
-                  size_t lev_half, cudaStream_t st) {
+template <typename T, bool TT>
+int corr_launches_t(const T* ser, int ns, int M, int L, long long n0, T* hist, double* acc64, double* acc64tt,
+                    T* lev, size_t lev_half, cudaStream_t st) {
     auto cl_of = [&](int l) { return (int)(((n0 + ns) >> l) - (n0 >> l)); };
     int launches = 0;
     const int grid = (M + ssk::kSliceChains - 1) / ssk::kSliceChains;
     const int last0 = (L == 1 || cl_of(1) == 0) ? 1 : 0;
-    ssk::corr_level0_kernel<T><<<grid, ssk::kCorrThreads, 0, st>>>(ser, ns, M, L, hist, acc64, last0);
+    ssk::corr_level0_kernel<T, TT><<<grid, ssk::kCorrThreads, 0, st>>>(ser, ns, M, L, hist, acc64, acc64tt, last0);
     if (cudaGetLastError() != cudaSuccess) return -1;
     ++launches;
     const T* yin = ser;
@@ -240,14 +241,22 @@ int corr_launches(const T* ser, int ns, int M, int L, long long n0, T* hist, dou
         if (cl == 0) break;
         T* yout = lev + (size_t)((l - 1) & 1) * lev_half;
         const int last = (l == L - 1 || cl_of(l + 1) == 0) ? 1 : 0;
-        ssk::corr_level_kernel<T><<<grid, ssk::kCorrThreads, 0, st>>>(yin, cprev, n0 >> (l - 1), n0 >> l, cl, l, M,
-                                                                     L, hist, yout, acc64, last);
+        ssk::corr_level_kernel<T, TT><<<grid, ssk::kCorrThreads, 0, st>>>(yin, cprev, n0 >> (l - 1), n0 >> l, cl, l,
+                                                                         M, L, hist, yout, acc64, acc64tt, last);
         if (cudaGetLastError() != cudaSuccess) return -1;
         ++launches;
         yin = yout;
         cprev = cl;
     }
     return launches;
+}
+
+// acc64tt null: channel TT off
+template <typename T>
+int corr_launches(const T* ser, int ns, int M, int L, long long n0, T* hist, double* acc64, double* acc64tt, T* lev,
+                  size_t lev_half, cudaStream_t st) {
+    return acc64tt ? corr_launches_t<T, true>(ser, ns, M, L, n0, hist, acc64, acc64tt, lev, lev_half, st)
+                   : corr_launches_t<T, false>(ser, ns, M, L, n0, hist, acc64, nullptr, lev, lev_half, st);
 }
 
 template <typename T, int W, int B>
@@ -340,7 +349,8 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     if (corr) {
         const T* ser = static_cast<const T*>(a.series) + (size_t)a.series_row0 * e.M * 6;
         const int nl = corr_launches<T>(ser, nsteps, e.M, c->levels, c->nsamp, static_cast<T*>(e.hist), e.acc64,
-                                        static_cast<T*>(e.lev), (size_t)(e.ser_cap / 2 + 1) * e.M * 6, c->stream);
+                                        e.acc64tt, static_cast<T*>(e.lev), (size_t)(e.ser_cap / 2 + 1) * e.M * 6,
+                                        c->stream);
         if (nl < 0) return fail(c, SS_ECUDA, "correlator kernel launch failed");
         c->launches += nl;
     }
@@ -413,6 +423,8 @@ int zero_observables(ss_ctx* c) {
         if (e.hist) SS_CUDA(c, cudaMemsetAsync(e.hist, 0, (size_t)e.M * c->levels * 96 * ts, c->stream));
         if (e.acc64)
             SS_CUDA(c, cudaMemsetAsync(e.acc64, 0, (size_t)e.slices * c->levels * 96 * sizeof(double), c->stream));
+        if (e.acc64tt)
+            SS_CUDA(c, cudaMemsetAsync(e.acc64tt, 0, (size_t)e.slices * c->levels * 48 * sizeof(double), c->stream));
         if (e.logs && c->P.max_logs > 0)
             SS_CUDA(c, cudaMemsetAsync(e.logs, 0, (size_t)c->P.max_logs * e.groups * 14 * sizeof(double),
                                        c->stream));
@@ -488,6 +500,23 @@ int set_state_t(ss_ctx* c, Elem& e, const double* R, const int32_t* Z, const int
 }
 
 // group sums [G][L][16][2][3] from the per-slice device sums
+// channel TT per group: out[G][L][16][3]
+int group_corr_tt(ss_ctx* c, Elem& e, std::vector<double>& out) {
+    const int L = c->levels;
+    std::vector<double> sl((size_t)e.slices * L * 48);
+    SS_CUDA(c, cudaMemcpyAsync(sl.data(), e.acc64tt, sl.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    out.assign((size_t)e.groups * L * 16 * 3, 0.0);
+    for (int s = 0; s < e.slices; ++s) {
+        const int g = (int)(((long long)s * e.groups) / e.slices);
+        for (int l = 0; l < L; ++l)
+            for (int d = 0; d < 3; ++d)
+                for (int lag = 0; lag < 16; ++lag)
+                    out[(((size_t)g * L + l) * 16 + lag) * 3 + d] += sl[((size_t)s * L + l) * 48 + d * 16 + lag];
+    }
+    return SS_OK;
+}
+
 int group_corr(ss_ctx* c, Elem& e, std::vector<double>& out) {
     const int L = c->levels;
     std::vector<double> sl((size_t)e.slices * L * 96);
@@ -1088,6 +1117,7 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
     if (!(p.dt * (4.0 * kb + ks) / p.zeta < 2.0))
         return fail(c, SS_EINVAL, "Euler step unstable: dt (4 k_b + k_s) / zeta must be < 2");
     if (p.create_mode != 0 && p.create_mode != 1) return fail(c, SS_EINVAL, "create_mode must be 0 or 1");
+    if (p.corr_tt != 0 && p.corr_tt != 1) return fail(c, SS_EINVAL, "corr_tt must be 0 or 1");
     if (p.destroy_new != 0 && p.destroy_new != 1) return fail(c, SS_EINVAL, "destroy_new must be 0 or 1");
     if (p.corr_levels > SS_MAX_LEVELS) return fail(c, SS_EINVAL, "corr_levels must be <= 32");
     if (p.groups < 1 || p.chunk_steps < 1 || p.log_every < 0 || p.max_logs < 0)
@@ -1125,6 +1155,7 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
             SS_CUDA(c, cudaMalloc(&e.ser, (size_t)e.M * 6 * e.ser_cap * ts));
             SS_CUDA(c, cudaMalloc(&e.lev, (size_t)2 * (e.ser_cap / 2 + 1) * e.M * 6 * ts));
             SS_CUDA(c, cudaMalloc(&e.acc64, (size_t)e.slices * c->levels * 96 * sizeof(double)));
+            if (p.corr_tt) SS_CUDA(c, cudaMalloc(&e.acc64tt, (size_t)e.slices * c->levels * 48 * sizeof(double)));
         }
         if (p.max_logs > 0) SS_CUDA(c, cudaMalloc(&e.logs, (size_t)p.max_logs * e.groups * 14 * sizeof(double)));
         e.flow_dirty = true;
@@ -1259,11 +1290,17 @@ int ss_stress(ss_ctx* c, int elem, double* t, double* mean, double* sem, int cap
 int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double* sem, int cap, int* n_out) {
     Elem* e = elem_at(c, elem);
     if (!e || cap < 0) return fail(c, SS_EINVAL, "bad element or capacity");
-    if (channel < SS_CH_AUTO || channel > SS_CH_TOTAL) return fail(c, SS_EINVAL, "bad channel");
+    if (channel < SS_CH_AUTO || channel > SS_CH_VIRTUAL) return fail(c, SS_EINVAL, "bad channel");
     if (!c->have_params || c->levels <= 0) return fail(c, SS_ESTATE, "correlator not enabled");
-    std::vector<double> acc;
+    const bool tt = channel == SS_CH_TT || channel == SS_CH_VIRTUAL;
+    if (tt && !e->acc64tt) return fail(c, SS_ESTATE, "channel TT needs corr_tt = 1");
+    std::vector<double> acc, acc_tt;
     int rc = group_corr(c, *e, acc);
     if (rc != SS_OK) return rc;
+    if (tt) {
+        rc = group_corr_tt(c, *e, acc_tt);
+        if (rc != SS_OK) return rc;
+    }
     const int L = c->levels, NG = e->groups;
     const double norm = (double)e->N * c->P.kT * c->P.kT;
     int n = 0;
@@ -1277,7 +1314,14 @@ int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double
                 for (int d = 0; d < 3; ++d) {
                     const double* base = &acc[((((size_t)g * L + l) * 16 + k) * 2) * 3];
                     const double auto_ = base[d], total = base[3 + d];
-                    v += channel == SS_CH_AUTO ? auto_ : (channel == SS_CH_TOTAL ? total : total - auto_);
+                    const double ttv = tt ? acc_tt[(((size_t)g * L + l) * 16 + k) * 3 + d] : 0.0;
+                    switch (channel) {
+                        case SS_CH_AUTO: v += auto_; break;
+                        case SS_CH_CROSS: v += total - auto_; break;
+                        case SS_CH_TOTAL: v += total; break;
+                        case SS_CH_TT: v += ttv; break;
+                        default: v += ttv - total; break;  // SS_CH_VIRTUAL
+                    }
                 }
                 v /= 3.0;
                 tot += v;
@@ -1398,6 +1442,19 @@ int ss_corr_sums(ss_ctx* c, int elem, double* acc, int* n_groups, int64_t* n_sam
     int rc = group_corr(c, *e, g);
     if (rc != SS_OK) return rc;
     if (acc) std::memcpy(acc, g.data(), g.size() * sizeof(double));
+    if (n_groups) *n_groups = e->groups;
+    if (n_samples) *n_samples = c->nsamp;
+    return SS_OK;
+}
+
+int ss_corr_sums_tt(ss_ctx* c, int elem, double* acc_tt, int* n_groups, int64_t* n_samples) {
+    Elem* e = elem_at(c, elem);
+    if (!e) return fail(c, SS_EINVAL, "bad element");
+    if (!c->have_params || c->levels <= 0 || !e->acc64tt) return fail(c, SS_ESTATE, "channel TT not enabled");
+    std::vector<double> g;
+    int rc = group_corr_tt(c, *e, g);
+    if (rc != SS_OK) return rc;
+    if (acc_tt) std::memcpy(acc_tt, g.data(), g.size() * sizeof(double));
     if (n_groups) *n_groups = e->groups;
     if (n_samples) *n_samples = c->nsamp;
     return SS_OK;
@@ -1661,7 +1718,7 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
         if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
         if (c->levels > 0 &&
             corr_launches<T>(static_cast<const T*>(a.series), ns, M, c->levels, done,
-                             reinterpret_cast<T*>(scr + off_hist), reinterpret_cast<double*>(scr + off_acc64),
+                             reinterpret_cast<T*>(scr + off_hist), reinterpret_cast<double*>(scr + off_acc64), nullptr,
                              reinterpret_cast<T*>(scr + off_lev), (size_t)(ser_cap / 2 + 1) * M * 6, st) < 0)
             return SS_ECUDA;
         done += ns;

@@ -1007,7 +1007,8 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
 // last level with new samples updates its own.  A CTA covers one slice of
 // kSliceChains chains and adds its chains' sums of this launch, in chain
 // order, to the slice's FP64 sums acc64 [slices][L][3][32] (component,
-// channel * 16 + lag).
+// channel * 16 + lag).  With TT the rows of sigma + sigma^(v) also take their
+// own samples as the later value (channel TT, acc64tt [slices][L][3][16]).
 constexpr int kCorrChainsPerWarp = 5;
 constexpr int kCorrWarps = (kSliceChains + kCorrChainsPerWarp - 1) / kCorrChainsPerWarp;  // 13
 constexpr int kCorrThreads = kCorrWarps * 32;
@@ -1015,6 +1016,26 @@ constexpr int kCorrMaxSteps = 1024;  // samples per launch (the level-sample buf
 
 // This slice's FP32 sums of one level (each thread's lags k0..15 of its row),
 // folded in chain order into FP64.
+// Channel TT of the rows q >= 3, folded the same way into out [3][16].
+template <typename T>
+__device__ __forceinline__ void corr_fold_slice_tt(const T (&acc2)[16], int k0, bool live, int slot, int q,
+                                                   double* __restrict__ out, T* red) {
+    __syncthreads();  // the first fold has read red
+    if (slot < kSliceChains && q >= 3) {
+        T* row = red + (size_t)slot * 48 + (q - 3) * kP;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k >= k0) row[k] = live ? acc2[k] : T(0);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 48; i += blockDim.x) {
+        if (i % kP < k0) continue;
+        double sum = 0.0;
+        for (int c = 0; c < kSliceChains; ++c) sum += (double)red[(size_t)c * 48 + i];
+        out[i] += sum;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void corr_fold_slice(const T (&acc)[16], int k0, bool live, int slot, int q,
                                                 double* __restrict__ out, T* red) {
@@ -1041,8 +1062,11 @@ __device__ __forceinline__ void corr_fold_slice(const T (&acc)[16], int k0, bool
 // Products of n new samples, sample j given by get(j) (a load, or a pair mean
 // that is also stored for the next level); nr returns the ring position of
 // the next sample (the number of samples in the last partial block).
-template <typename T, int K0, typename Get>
-__device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], Get get, int n, int src_lane, int& nr) {
+// With TT, acc2 also takes the row's own sample as the later value (for the
+// rows of sigma + sigma^(v): channel TT).
+template <typename T, int K0, bool TT, typename Get>
+__device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], T (&acc2)[16], Get get, int n,
+                                                   int src_lane, int& nr) {
     int j = 0;
     for (; j + 16 <= n; j += 16) {
         T yv[16];
@@ -1054,6 +1078,10 @@ __device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], Get
             r[u] = yv[u];
 #pragma unroll
             for (int k = K0; k < 16; ++k) acc[k] += xv * r[(u - k) & 15];
+            if constexpr (TT) {
+#pragma unroll
+                for (int k = K0; k < 16; ++k) acc2[k] += yv[u] * r[(u - k) & 15];
+            }
         }
     }
     const int rem = n - j;
@@ -1065,6 +1093,10 @@ __device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], Get
             r[u] = yv;
 #pragma unroll
             for (int k = K0; k < 16; ++k) acc[k] += xv * r[(u - k) & 15];
+            if constexpr (TT) {
+#pragma unroll
+                for (int k = K0; k < 16; ++k) acc2[k] += yv * r[(u - k) & 15];
+            }
         }
     }
     nr = rem;
@@ -1084,10 +1116,10 @@ __device__ __forceinline__ void corr_ring_newest(const T (&r)[16], int nr, T* ou
     }
 }
 
-template <typename T>
+template <typename T, bool TT>
 __global__ void __launch_bounds__(kCorrThreads)
     corr_level0_kernel(const T* __restrict__ ser, int ns, int M, int L, T* __restrict__ hist,
-                       double* __restrict__ acc64, int last) {
+                       double* __restrict__ acc64, double* __restrict__ acc64tt, int last) {
     __shared__ T red[kSliceChains * 96];
     const int lane = threadIdx.x & 31;
     const int cc = lane / 6, q = lane % 6;
@@ -1097,17 +1129,22 @@ __global__ void __launch_bounds__(kCorrThreads)
     const int mm = live ? m : 0;
     const int src_lane = cc * 6 + q % 3;
     T* h = hist + (((size_t)mm * L) * 6 + q) * 16;
-    T r[16], acc[16];
+    T r[16], acc[16], acc2[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         r[i] = live ? h[i] : T(0);
         acc[i] = T(0);
+        acc2[i] = T(0);
     }
     int nr = 0;
     const T* yrow = ser + (size_t)mm * 6 + q;
     const size_t stride = (size_t)M * 6;
-    corr_ring_products<T, 0>(r, acc, [&](int j) { return yrow[(size_t)j * stride]; }, ns, min(src_lane, 31), nr);
+    corr_ring_products<T, 0, TT>(r, acc, acc2, [&](int j) { return yrow[(size_t)j * stride]; }, ns,
+                                 min(src_lane, 31), nr);
     corr_fold_slice(acc, 0, live, lane < 30 ? slot : kSliceChains, q, acc64 + ((size_t)blockIdx.x * L) * 96, red);
+    if constexpr (TT)
+        corr_fold_slice_tt(acc2, 0, live, lane < 30 ? slot : kSliceChains, q,
+                           acc64tt + ((size_t)blockIdx.x * L) * 48, red);
     if (!live) return;
     if (last) {
         T nh[16];
@@ -1120,10 +1157,11 @@ __global__ void __launch_bounds__(kCorrThreads)
 // Level l >= 1 from the cprev level-(l-1) samples of this launch, yin
 // [cprev][M][6] (absolute indices pb .. pb + cprev - 1); writes the cl new
 // level-l samples to yout [cl][M][6] (absolute indices nb ..).
-template <typename T>
+template <typename T, bool TT>
 __global__ void __launch_bounds__(kCorrThreads)
     corr_level_kernel(const T* __restrict__ yin, int cprev, long long pb, long long nb, int cl, int l, int M,
-                      int L, T* __restrict__ hist, T* __restrict__ yout, double* __restrict__ acc64, int last) {
+                      int L, T* __restrict__ hist, T* __restrict__ yout, double* __restrict__ acc64,
+                      double* __restrict__ acc64tt, int last) {
     __shared__ T red[kSliceChains * 96];
     const int lane = threadIdx.x & 31;
     const int cc = lane / 6, q = lane % 6;
@@ -1160,16 +1198,20 @@ __global__ void __launch_bounds__(kCorrThreads)
     };
     // lag products of level l over its new samples
     T* h = hist + (((size_t)mm * L + l) * 6 + q) * 16;
-    T r[16], acc[16];
+    T r[16], acc[16], acc2[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         r[i] = live ? h[i] : T(0);
         acc[i] = T(0);
+        acc2[i] = T(0);
     }
     int nr = 0;
-    corr_ring_products<T, kP / 2>(r, acc, mean, cl, src_lane, nr);
+    corr_ring_products<T, kP / 2, TT>(r, acc, acc2, mean, cl, src_lane, nr);
     corr_fold_slice(acc, kP / 2, live, lane < 30 ? slot : kSliceChains, q,
                     acc64 + ((size_t)blockIdx.x * L + l) * 96, red);
+    if constexpr (TT)
+        corr_fold_slice_tt(acc2, kP / 2, live, lane < 30 ? slot : kSliceChains, q,
+                           acc64tt + ((size_t)blockIdx.x * L + l) * 48, red);
     if (!live) return;
     if (last) {
         T nh[16];

@@ -1,0 +1,91 @@
+"""Channel TT of the correlator and the virtual-stress share (GPU).
+
+* Channel TT (later and origin both sigma + sigma^(v)) in FP64 equals the
+  oracle's sums on the same chains and random numbers; enabling it leaves the
+  AUTO and TOTAL sums bit for bit unchanged.
+* The relative virtual-stress contribution of Sec. 4.2 (Eq.
+  relative_contribution_virtual_stress_to_shear_relaxation_modulus),
+  VIRTUAL / TOTAL with VIRTUAL = TT - TOTAL, at N = 40: the paper reports it
+  as roughly 25% and not strongly time dependent; printed numbers of the paper
+  are checked as +-30% sanity values.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import Params
+from paper_1106_2899_gb300 import SlipSpring
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu(cuda_ok):
+    from paper_1106_2899_gb300 import build
+    build.build()
+    yield
+
+
+def _run(M, N, precision, levels, steps, tt, seed=5):
+    g = SlipSpring([(M, N)], precision=precision, seed=seed)
+    g.set_params(**synth.PAPER, corr_levels=levels, groups=4, corr_tt=tt)
+    g.run(steps)
+    assert g.status() == 0
+    return g
+
+
+def test_tt_channel_fp64_matches_oracle_and_leaves_other_channels_unchanged():
+    M, N, levels, steps = 128, 24, 8, 1500  # 1024 + 476: a ragged second launch
+    g1 = _run(M, N, "fp64", levels, steps, 1)
+    g0 = _run(M, N, "fp64", levels, steps, 0)
+    a1, n1 = g1.corr_sums()
+    a0, n0 = g0.corr_sums()
+    assert n1 == n0 == steps
+    assert np.array_equal(a1, a0)
+    tt, ntt = g1.corr_sums_tt()
+    assert ntt == steps
+    o = oracle.Ensemble(Params(N=N, **synth.PAPER), seed=5, M=M, groups=1, levels=levels)
+    o.init()
+    o.run(steps)
+    ott = o.corr_sums_tt()[0]  # [levels][16][3]
+    oacc = o.corr_sums()[0][0]
+    got = tt.sum(axis=0)
+    mask = np.zeros((levels, 16), bool)
+    mask[0, :] = True
+    mask[1:, 8:] = True
+    scale = np.abs(ott[mask]).max()
+    assert np.allclose(got[mask], ott[mask], rtol=1e-9, atol=1e-12 * scale)
+    assert np.allclose(a1.sum(axis=0)[mask], oacc[mask], rtol=1e-9, atol=1e-12 * np.abs(oacc[mask]).max())
+    # readout: VIRTUAL = TT - TOTAL per slot
+    t, Gtt, _ = g1.correlator("tt")
+    _, Gtot, _ = g1.correlator("total")
+    _, Gv, _ = g1.correlator("virtual")
+    assert np.allclose(Gv, Gtt - Gtot, rtol=1e-12, atol=1e-14)
+
+
+def test_channel_tt_needs_the_flag():
+    g = _run(64, 16, "fp32", 4, 10, 0)
+    with pytest.raises(Exception):
+        g.correlator("virtual")
+
+
+@pytest.mark.slow
+def test_virtual_stress_share_at_N40_is_about_a_quarter():
+    M, N, levels = 65536, 40, 16
+    g = SlipSpring([(M, N)], precision="fp32", seed=40)
+    g.set_params(**synth.PAPER, corr_levels=levels, groups=32, corr_tt=1)
+    g.run(5000)
+    g.reset_observables()
+    g.run(60000)
+    assert g.status() == 0
+    t, Gtot, stot = g.correlator("total")
+    _, Gv, sv = g.correlator("virtual")
+    ok = (Gtot > 0) & (stot < 0.05 * Gtot) & (np.abs(sv) < 0.1 * np.abs(Gv) + 1e-12) & (t >= 1.0)
+    share = Gv[ok] / Gtot[ok]
+    print("\nvirtual-stress share at N=40: t in [%.3g, %.3g], share %s"
+          % (t[ok].min(), t[ok].max(), np.array2string(share[::4], precision=3)))
+    assert ok.sum() >= 20
+    # the paper: roughly 25%, not strongly time dependent (+-30% sanity band)
+    assert 0.175 <= np.median(share) <= 0.325, np.median(share)
+    assert share.max() / share.min() < 1.6, (share.min(), share.max())
