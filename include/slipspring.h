@@ -63,7 +63,8 @@ extern "C" {
 
 #define SS_CORR_POINTS 16 /* multiple-tau points per level */
 #define SS_MAX_LEVELS 32
-#define SS_MAX_BEADS 64   /* chain length limit of this build             */
+#define SS_MAX_BEADS 128  /* chain length limit of this build             */
+#define SS_MAX_SLOTS 64   /* slip-springs per chain: z_max <= min(N, 64)  */
 
 typedef struct ss_ctx ss_ctx;
 
@@ -88,7 +89,8 @@ typedef struct {
     double k_s;     /* slip-spring stiffness; 0 -> 3 kT / (Ns b^2)                        */
     int32_t create_mode;    /* 0: K = z_max - Z creation attempts per end (GPU form of
                                Sec. 3.2); 1: K = 1 (CPU form) [0]                        */
-    int32_t z_max;          /* slip-spring slots per chain, 1..N [N]                     */
+    int32_t z_max;          /* slip-spring slots per chain, 1..min(N, SS_MAX_SLOTS)
+                               [min(N, SS_MAX_SLOTS)]                                    */
     int32_t destroy_new;    /* 1: a spring created in a step may be destroyed in the same
                                step; 0: only springs that existed before [0]             */
     int32_t recenter_every; /* shift each chain and its anchors to the chain's centre of
@@ -119,7 +121,7 @@ int ss_create(ss_ctx** out, const ss_element* elems, int n_elems, int precision,
 
 /* Validate and apply parameters; allocates the device state.  Must precede the
  * first ss_run.  Validation: every physical parameter finite and > 0 (N0 may
- * be +inf), Euler stability dt (4 k_b + k_s)/zeta < 2, 1 <= z_max <= N.
+ * be +inf), Euler stability dt (4 k_b + k_s)/zeta < 2, 1 <= z_max <= min(N, SS_MAX_SLOTS).
  * Calling it again resets the state, the observables and the step counter. */
 int ss_set_params(ss_ctx* ctx, const ss_params* p);
 

@@ -13,6 +13,7 @@ ERRORS = {-1: "SS_EINVAL", -2: "SS_ENOMEM", -3: "SS_ECUDA", -4: "SS_EOVERFLOW", 
           -6: "SS_ETIMEOUT", -7: "SS_ETOOBIG"}
 SS_NOALLOC_SCRATCH_BYTES = 32 << 20
 SS_FP32, SS_FP64 = 0, 1
+SS_MAX_BEADS, SS_MAX_SLOTS = 128, 64
 SS_CH_AUTO, SS_CH_CROSS, SS_CH_TOTAL, SS_CH_TT, SS_CH_VIRTUAL = 0, 1, 2, 3, 4
 
 # every symbol include/slipspring.h declares

@@ -126,7 +126,7 @@ class SlipSpring:
     # ------------------------------------------------------------ state ---
     def _zm(self, elem):
         zm = (self.params or {}).get("z_max", 0)
-        return zm if zm > 0 else self.elements[elem][1]
+        return zm if zm > 0 else min(self.elements[elem][1], nat.SS_MAX_SLOTS)
 
     def get_state(self, elem=0):
         M, N = self.elements[elem]

@@ -161,12 +161,17 @@ void layout_for(int N, int* W, int* B) {
             *W = 16, *B = 2;
     } else if (N <= 48) {
         *W = 16, *B = 3;
-    } else {
+    } else if (N <= 64) {
         *W = 16, *B = 4;
+    } else {
+        *W = 32, *B = 4;
     }
 }
 
 int chains_per_cta(int W) { return kWarpsPerCta * (32 / W); }
+
+// z_max by default: one slot per bead (Sec. 3.2), at most SS_MAX_SLOTS
+int default_zmax(int N) { return std::min(N, SS_MAX_SLOTS); }
 
 // Inverse standard normal CDF by bisection on erfc: the destruction
 // threshold on a standard normal draw (host constant).
@@ -202,7 +207,7 @@ ssk::StepConst<T> step_const(const ss_ctx* c, int N) {
     s.NkT = T((double)N * p.kT);
     s.kT = T(p.kT);
     s.pc[0] = T(0);
-    for (int K = 1; K <= ssk::kMaxBeads; ++K) {
+    for (int K = 1; K <= ssk::kMaxSlots; ++K) {
         double pc = p.dt * p.kT / (p.zeta_s * p.N0 * (double)K);
         if (pc > 0.5) pc = 0.5;
         s.pc[K] = T(pc);
@@ -359,7 +364,7 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
 
 template <typename T>
 int dispatch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
-    if (e.W == 32) return launch_chunk<T, 32, 1>(c, e, t0, nsteps);
+    if (e.W == 32) return e.B == 4 ? launch_chunk<T, 32, 4>(c, e, t0, nsteps) : launch_chunk<T, 32, 1>(c, e, t0, nsteps);
     switch (e.B) {
         case 1: return launch_chunk<T, 16, 1>(c, e, t0, nsteps);
         case 2: return launch_chunk<T, 16, 2>(c, e, t0, nsteps);
@@ -388,9 +393,13 @@ int launch_init(ss_ctx* c, Elem& e) {
             ssk::init_kernel<T, 48><<<blocks, 128, 0, c->stream>>>((T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb,
                                                                    sa, lam, k0, k1, e.chain_base);
             break;
-        default:
+        case 64:
             ssk::init_kernel<T, 64><<<blocks, 128, 0, c->stream>>>((T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax, sb,
                                                                    sa, lam, k0, k1, e.chain_base);
+            break;
+        default:
+            ssk::init_kernel<T, 128><<<blocks, 128, 0, c->stream>>>((T*)e.R, (T*)e.A, e.S, e.Z, e.M, e.N, e.zmax,
+                                                                    sb, sa, lam, k0, k1, e.chain_base);
     }
     SS_CUDA(c, cudaGetLastError());
     c->launches++;
@@ -546,9 +555,9 @@ int chains_in_group(const Elem& e, int g) {
 
 // ------------------------------------------------------------ batched ----
 // Lane layouts the batched path can use; one persistent kernel per layout.
-constexpr int kBatchedLayouts = 5;
-constexpr int kLayoutW[kBatchedLayouts] = {16, 16, 16, 32, 8};
-constexpr int kLayoutB[kBatchedLayouts] = {1, 2, 3, 1, 2};
+constexpr int kBatchedLayouts = 7;
+constexpr int kLayoutW[kBatchedLayouts] = {16, 16, 16, 32, 8, 16, 32};
+constexpr int kLayoutB[kBatchedLayouts] = {1, 2, 3, 1, 2, 4, 4};
 
 int layout_class(int W, int B) {
     for (int k = 0; k < kBatchedLayouts; ++k)
@@ -632,7 +641,9 @@ const void* batched_fn_of(int k) {
         case 1: return batched_fn<T, 16, 2>();
         case 2: return batched_fn<T, 16, 3>();
         case 3: return batched_fn<T, 32, 1>();
-        default: return batched_fn<T, 8, 2>();
+        case 4: return batched_fn<T, 8, 2>();
+        case 5: return batched_fn<T, 16, 4>();
+        default: return batched_fn<T, 32, 4>();
     }
 }
 
@@ -708,7 +719,7 @@ int autotune(ss_ctx* c) {
                 t.W = bestW;
                 t.B = bestB;
                 t.NP = t.W * t.B;
-                t.zmax = c->P.z_max > 0 ? std::min(c->P.z_max, N) : N;
+                t.zmax = c->P.z_max > 0 ? std::min(c->P.z_max, N) : default_zmax(N);
                 t.slices = (t.M + ssk::kSliceChains - 1) / ssk::kSliceChains;
                 t.groups = 1;
                 const size_t ts = sizeof(T);
@@ -953,7 +964,7 @@ int launch_adjoint(ss_ctx* c, Elem& e, int seg) {
 
 template <typename T>
 int dispatch_adjoint(ss_ctx* c, Elem& e, int seg) {
-    if (e.W == 32) return launch_adjoint<T, 32, 1>(c, e, seg);
+    if (e.W == 32) return e.B == 4 ? launch_adjoint<T, 32, 4>(c, e, seg) : launch_adjoint<T, 32, 1>(c, e, seg);
     switch (e.B) {
         case 1: return launch_adjoint<T, 16, 1>(c, e, seg);
         case 2: return launch_adjoint<T, 16, 2>(c, e, seg);
@@ -1124,8 +1135,8 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
         return fail(c, SS_EINVAL, "groups, chunk_steps must be >= 1; log_every, max_logs >= 0");
     if (p.log_every > 0 && p.max_logs <= 0) return fail(c, SS_EINVAL, "log_every > 0 needs max_logs > 0");
     for (const Elem& e : c->el) {
-        const int zm = p.z_max > 0 ? p.z_max : e.N;
-        if (zm < 1 || zm > e.N) return fail(c, SS_EINVAL, "z_max must be in 1..N");
+        const int zm = p.z_max > 0 ? p.z_max : default_zmax(e.N);
+        if (zm < 1 || zm > std::min(e.N, SS_MAX_SLOTS)) return fail(c, SS_EINVAL, "z_max must be in 1..min(N, 64)");
     }
     if (c->counters) cudaStreamSynchronize(c->stream);
     for (Elem& e : c->el) free_elem(e);
@@ -1141,7 +1152,7 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
     if (c->levels > 0) c->P.chunk_steps = std::min(c->P.chunk_steps, ssk::kCorrMaxSteps);
     const size_t ts = tsize(c);
     for (Elem& e : c->el) {
-        e.zmax = p.z_max > 0 ? p.z_max : e.N;
+        e.zmax = p.z_max > 0 ? p.z_max : default_zmax(e.N);
         e.slices = (e.M + ssk::kSliceChains - 1) / ssk::kSliceChains;
         e.groups = std::min(p.groups, e.slices);
         SS_CUDA(c, cudaMalloc(&e.R, (size_t)e.M * 3 * e.NP * ts));
@@ -1775,8 +1786,8 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
         if ((q.create_mode != 0 && q.create_mode != 1) || (q.destroy_new != 0 && q.destroy_new != 1))
             return SS_EINVAL;
         if (q.corr_levels > SS_MAX_LEVELS || q.chunk_steps < 1) return SS_EINVAL;
-        const int zm = q.z_max > 0 ? q.z_max : n_beads;
-        if (zm < 1 || zm > n_beads) return SS_EINVAL;
+        const int zm = q.z_max > 0 ? q.z_max : default_zmax(n_beads);
+        if (zm < 1 || zm > std::min(n_beads, SS_MAX_SLOTS)) return SS_EINVAL;
         c.P = q;
         c.k_b = kb;
         c.k_s = ks;
@@ -1837,13 +1848,15 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
     &c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A, S, Z, scr, off_hist, off_ser, off_lev,       \
         ser_cap, off_acc64, off_kap, off_kfrom, off_cnt, off_status, st
     if (precision == SS_FP64) {
-        if (e.W == 32) rc = noalloc_launches<double, 32, 1>(SS_NOALLOC_ARGS);
+        if (e.W == 32 && e.B == 4) rc = noalloc_launches<double, 32, 4>(SS_NOALLOC_ARGS);
+        else if (e.W == 32) rc = noalloc_launches<double, 32, 1>(SS_NOALLOC_ARGS);
         else if (e.B == 1) rc = noalloc_launches<double, 16, 1>(SS_NOALLOC_ARGS);
         else if (e.B == 2) rc = noalloc_launches<double, 16, 2>(SS_NOALLOC_ARGS);
         else if (e.B == 3) rc = noalloc_launches<double, 16, 3>(SS_NOALLOC_ARGS);
         else rc = noalloc_launches<double, 16, 4>(SS_NOALLOC_ARGS);
     } else {
-        if (e.W == 32) rc = noalloc_launches<float, 32, 1>(SS_NOALLOC_ARGS);
+        if (e.W == 32 && e.B == 4) rc = noalloc_launches<float, 32, 4>(SS_NOALLOC_ARGS);
+        else if (e.W == 32) rc = noalloc_launches<float, 32, 1>(SS_NOALLOC_ARGS);
         else if (e.B == 1) rc = noalloc_launches<float, 16, 1>(SS_NOALLOC_ARGS);
         else if (e.B == 2) rc = noalloc_launches<float, 16, 2>(SS_NOALLOC_ARGS);
         else if (e.B == 3) rc = noalloc_launches<float, 16, 3>(SS_NOALLOC_ARGS);

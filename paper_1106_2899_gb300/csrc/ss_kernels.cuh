@@ -5,7 +5,8 @@
 // Layout: one chain per W-lane segment of a warp (W = 32: one chain per warp,
 // W = 16: two), B beads per lane: lane l of a segment owns beads and
 // slip-spring slots l, l + W, ..., so N <= W*B and z_max <= N (the paper's
-// one-slot-per-bead bound, Sec. 3.2).  A launch advances each chain `nsteps`
+// one-slot-per-bead bound, Sec. 3.2); slots above 64 stay empty (z_max <= 64,
+// so a 64-bit mask covers a bead's springs).  A launch advances each chain `nsteps`
 // steps with its whole state in registers; neighbouring beads are read from a
 // per-warp shared-memory position table, stresses are reduced with shuffles.
 //
@@ -28,7 +29,8 @@ constexpr int kCells = 32;  // (channel, lag) cells per level and component: cha
 constexpr uint32_t kPurposeStep = 1, kPurposeCreate = 2, kPurposeInitBond = 3,
                    kPurposeInitZ = 4, kPurposeInitS = 5, kPurposeInitA = 6;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxBeads = 64;
+constexpr int kMaxBeads = 128;  // beads per chain
+constexpr int kMaxSlots = 64;   // slip-spring slots per chain (z_max <= min(N, kMaxSlots))
 constexpr int kSliceChains = 64;  // chains per FP64 correlator/log slice
 constexpr int kMaxCorrLevels = 32;  // correlator levels the library accepts
 
@@ -182,7 +184,7 @@ struct StepConst {
     T sa;         // sqrt(kT / k_s): anchor spread of a new spring
     T cd;         // Phi^{-1}(min(dt kT/zeta_s, 1)) (+inf when that is 1)
     T NkT, kT;
-    T pc[kMaxBeads + 1];  // creation probability per end and attempt, by K
+    T pc[kMaxSlots + 1];  // creation probability per end and attempt, by K
     T two_pref;           // 2 dt kT / zeta_s
     T c2;                 // 2 chop log2(e): base-2 exponent per change of squared length
     uint32_t rk0[10], rk1[10];  // Philox round keys (key + r * Weyl increment)

@@ -7,6 +7,9 @@
   K comparisons the family-wise 1% bound is about 4 SE; every z must be below 4,
   95% of them below 3, and where the oracle is resolved to 0.5% the two agree
   within 2%.
+* Steady shear at N = 80 (Sec. 4.1): the average number of slip-springs the
+  paper prints for gdot = 0.01, 0.1, 1 (8.7, 4.2, 1.6, against 20 at
+  equilibrium), within 15% (measured: 8.6, 4.2, 1.7).
 * Linear response (Sec. 2.3, Eqs. single_chain_time_depending_stress_expression_final
   and relaxation_modulus_tensor_green_kubo_form): for a step of simple shear
   of small rate, eta+(t) = integral_0^t G_TOTAL(s) ds, with G_TOTAL = AUTO +
@@ -154,3 +157,26 @@ def test_linear_response_eta_plus_is_integral_of_G_total():
             assert abs(em - am) > 4 * comb, (T, em, am, comb)
         checked += 1
     assert checked == 4
+
+
+@pytest.mark.slow
+def test_steady_shear_number_of_slip_springs_at_N80():
+    # the spring number relaxes slowly (at gdot = 1 it settles after ~4e5 steps):
+    # 1e6 steps, the second half averaged
+    N, M, steps, log_every = 80, 1024, 1000000, 20000
+    printed = {0.01: 8.7, 0.1: 4.2, 1.0: 1.6}
+    rates = list(printed)
+    g = SlipSpring([(M, N)] * len(rates), precision="fp32", seed=80)
+    g.set_params(**synth.PAPER, corr_levels=-1, groups=8, log_every=log_every, max_logs=steps // log_every)
+    for e, gd in enumerate(rates):
+        g.set_flow(synth.shear_kappa(gd), 0, elem=e)
+    g.run(steps)
+    assert g.status() == 0
+    got = {}
+    for e, gd in enumerate(rates):
+        t, L = g.log_sums(e)
+        z = L[:, :, 12].sum(axis=1) / M  # <Z> at each log
+        got[gd] = z[len(z) // 2:].mean()  # steady state: the second half
+        assert abs(got[gd] - printed[gd]) <= 0.15 * printed[gd], (gd, got[gd], printed[gd])
+    print("\nsteady shear, N=80: <Z> = %s (paper: %s)" % (
+        {k: round(v, 2) for k, v in got.items()}, printed))

@@ -148,7 +148,7 @@ def test_fp64_parity_workload_bit_exact_integers():
 
 
 @pytest.mark.parametrize("case", ["N2", "zmax1", "no_springs", "cpu_mode", "destroy_new", "M1",
-                                  "ragged", "fast_create", "N48", "N64", "N33_crowded"])
+                                  "ragged", "fast_create", "N48", "N64", "N33_crowded", "N80", "N128_zcap"])
 def test_fp64_edge_cases(case):
     kw = dict(N=16)
     M = 37
@@ -175,6 +175,10 @@ def test_fp64_edge_cases(case):
         kw = dict(N=64, N0=2.0)  # four beads per lane, up to 64 springs
     elif case == "N33_crowded":
         kw = dict(N=33, N0=0.6)  # sub-slots beyond the first 16 are occupied
+    elif case == "N80":
+        kw = dict(N=80, z_max=64)  # 32 lanes x 4 beads (the paper's longest chains)
+    elif case == "N128_zcap":
+        kw = dict(N=128, z_max=64, N0=2.0)  # <Z> pressed against the 64-slot cap
     p = Params(**kw)
     _fp64_stepwise(p, M, seed=17, steps_each=1, blocks=150)
 

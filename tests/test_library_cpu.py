@@ -39,7 +39,7 @@ def test_argument_validation_without_device(lib):
     h = C.c_void_p()
     el = (nat.ss_element * 1)(nat.ss_element(4, 1))  # N = 1 is not a chain
     assert lib.ss_create(C.byref(h), el, 1, nat.SS_FP32, 0, None) == -1
-    el = (nat.ss_element * 1)(nat.ss_element(4, 65))  # longer than this build supports
+    el = (nat.ss_element * 1)(nat.ss_element(4, 129))  # longer than this build supports
     assert lib.ss_create(C.byref(h), el, 1, nat.SS_FP32, 0, None) == -1
     el = (nat.ss_element * 1)(nat.ss_element(4, 16))
     assert lib.ss_create(C.byref(h), el, 1, 7, 0, None) == -1  # bad precision
