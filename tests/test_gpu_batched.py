@@ -54,7 +54,8 @@ def _ctx(els, precision, log_every, max_logs, batched):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_batched_equals_per_element_path(precision):
-    els = [(100, 16), (77, 24), (130, 32), (65, 48), (9, 20), (200, 32)]
+    # every lane layout of the batched launch: 16x1, 16x2, 16x3, 16x4, 32x4
+    els = [(100, 16), (77, 24), (130, 32), (65, 48), (9, 20), (200, 32), (40, 64), (33, 80)]
     elem, frm, kap = _flow_table([m for m, _ in els], 3, 150, seed=1)
     steps, log_every = 500, 50
     out = {}
