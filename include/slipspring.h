@@ -284,10 +284,13 @@ int ss_window_backward(ss_ctx* ctx, const double* dL_dG, double grad[3]);
  * call cudaMalloc: code that runs while a CUDA graph is being captured, code
  * inside a host that owns all device memory through its own pool, and
  * real-time loops where an allocation could block.  It advances caller-owned
- * device state by n_steps with the same chain kernel as ss_run, and keeps the
- * kernel's working memory (correlator history, per-block partial sums, event
+ * device state by n_steps with the same chain and correlator kernels as
+ * ss_run, and keeps their working memory (correlator history and FP64 sums,
+ * the stress series of a launch and the correlator's level samples, event
  * counters, the flow) in one file-scope device array of SS_NOALLOC_SCRATCH_BYTES
  * bytes that every GPU which loads the library holds until the process exits.
+ * The series takes what the rest leaves, so the launch length shrinks as
+ * n_chains grows.
  * It calls no cudaMalloc, cudaFree or allocating library routine.
  *
  * State (device pointers, read and written in place), with NP = n_beads
@@ -296,7 +299,7 @@ int ss_window_backward(ss_ctx* ctx, const double* dL_dG, double grad[3]);
  *   SS_FP64; entries beyond n_beads / beyond Z are ignored), S [n_chains][NP]
  *   int32 bead index of slot j (j < Z), Z [n_chains] int32.
  * params: as ss_set_params (log_every must be 0; chunk_steps splits the call
- *   into launches); z_max <= n_beads.  kappa: row-major constant velocity
+ *   into launches; channel TT is not accumulated); z_max <= min(n_beads, 64).  kappa: row-major constant velocity
  *   gradient for the whole call (host array), NULL for none.
  * seed, chain_base, t0: Philox key, global id of chain 0 and the index of the
  *   first step, so that consecutive calls with t0 advanced by n_steps draw the
@@ -308,7 +311,8 @@ int ss_window_backward(ss_ctx* ctx, const double* dL_dG, double grad[3]);
  *   bead position was produced.
  * Errors: SS_EINVAL for invalid arguments, SS_ETOOBIG when the request needs
  *   more scratch than SS_NOALLOC_SCRATCH_BYTES (it grows with n_chains and
- *   corr_levels), SS_EOVERFLOW if t0 + n_steps passes 2^32, SS_ECUDA.
+ *   corr_levels; with the correlator on, at least one step of series must fit),
+ *   SS_EOVERFLOW if t0 + n_steps passes 2^32, SS_ECUDA.
  * The first call on a device looks up the device address of the array (with
  *   that device current) and caches it; make that first call before any stream
  *   capture.  Every call, on any stream, uses the same array and leaves its
