@@ -224,36 +224,17 @@ ssk::StepConst<T> step_const(const ss_ctx* c, int N) {
     return s;
 }
 
-// Correlator kernels of one launch: level 0 on the launch's series (ns rows
-// of [M][6]), then one kernel per higher level that completes a sample; each
-// CTA folds its slice's sums into acc64.  n0: samples before the launch; lev:
-// two level-sample buffers of lev_half elements.  Returns the number of
-// kernels launched, or -1.
+// The correlator kernel of one launch: all levels over the launch's series
+// (ns rows of [M][6]); each CTA folds its slice's sums into acc64.  n0:
+// samples before the launch; lev: two level-sample buffers of lev_half
+// elements.  Returns the number of kernels launched, or -1.
 template <typename T, bool TT>
 int corr_launches_t(const T* ser, int ns, int M, int L, long long n0, T* hist, double* acc64, double* acc64tt,
                     T* lev, size_t lev_half, cudaStream_t st) {
-    auto cl_of = [&](int l) { return (int)(((n0 + ns) >> l) - (n0 >> l)); };
-    int launches = 0;
     const int grid = (M + ssk::kSliceChains - 1) / ssk::kSliceChains;
-    const int last0 = (L == 1 || cl_of(1) == 0) ? 1 : 0;
-    ssk::corr_level0_kernel<T, TT><<<grid, ssk::kCorrThreads, 0, st>>>(ser, ns, M, L, hist, acc64, acc64tt, last0);
-    if (cudaGetLastError() != cudaSuccess) return -1;
-    ++launches;
-    const T* yin = ser;
-    int cprev = ns;
-    for (int l = 1; l < L; ++l) {
-        const int cl = cl_of(l);
-        if (cl == 0) break;
-        T* yout = lev + (size_t)((l - 1) & 1) * lev_half;
-        const int last = (l == L - 1 || cl_of(l + 1) == 0) ? 1 : 0;
-        ssk::corr_level_kernel<T, TT><<<grid, ssk::kCorrThreads, 0, st>>>(yin, cprev, n0 >> (l - 1), n0 >> l, cl, l,
-                                                                         M, L, hist, yout, acc64, acc64tt, last);
-        if (cudaGetLastError() != cudaSuccess) return -1;
-        ++launches;
-        yin = yout;
-        cprev = cl;
-    }
-    return launches;
+    ssk::corr_kernel<T, TT><<<grid, ssk::kCorrThreads, 0, st>>>(ser, ns, n0, M, L, hist, lev, lev_half, acc64,
+                                                                acc64tt);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 // acc64tt null: channel TT off

@@ -1003,10 +1003,10 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
 // Samples of a level are [j][M][6] arrays (the chain kernel's series for
 // level 0).  hist [M][L][6][16] keeps the newest 16 samples of every level
 // and row (oldest first, zero after a reset): the lags reach back into
-// earlier launches through a 16-entry register ring.  Level l's kernel also
-// brings level l-1's history up to date (it needs the old newest sample of
-// level l-1 for a pair that straddles the launch boundary); the kernel of the
-// last level with new samples updates its own.  A CTA covers one slice of
+// earlier launches through a 16-entry register ring.  Level l also brings
+// level l-1's history up to date (it needs the old newest sample of level l-1
+// for a pair that straddles the launch boundary); the last level with new
+// samples updates its own.  A CTA covers one slice of
 // kSliceChains chains and adds its chains' sums of this launch, in chain
 // order, to the slice's FP64 sums acc64 [slices][L][3][32] (component,
 // channel * 16 + lag).  With TT the rows of sigma + sigma^(v) also take their
@@ -1041,7 +1041,8 @@ __device__ __forceinline__ void corr_fold_slice_tt(const T (&acc2)[16], int k0, 
 template <typename T>
 __device__ __forceinline__ void corr_fold_slice(const T (&acc)[16], int k0, bool live, int slot, int q,
                                                 double* __restrict__ out, T* red) {
-    // red: [kSliceChains][96] T in shared memory
+    // red: [kSliceChains][96] T in shared memory, free once every thread is here
+    __syncthreads();
     if (slot < kSliceChains) {
         T* row = red + (size_t)slot * 96 + (q % 3) * kCells + (q / 3) * kP;
 #pragma unroll
@@ -1118,108 +1119,108 @@ __device__ __forceinline__ void corr_ring_newest(const T (&r)[16], int nr, T* ou
     }
 }
 
+// All levels of one launch in one kernel: level 0 on the launch's series
+// (ns rows of [M][6]), then each higher level that completes a sample, its
+// samples formed as pairwise means of the level below while they are read and
+// stored for the next level in the ping-pong buffers lev (lev_half elements
+// each).  Every thread reads only rows it wrote itself (its chain and series
+// row); the block synchronises only for the slice folds.
 template <typename T, bool TT>
 __global__ void __launch_bounds__(kCorrThreads)
-    corr_level0_kernel(const T* __restrict__ ser, int ns, int M, int L, T* __restrict__ hist,
-                       double* __restrict__ acc64, double* __restrict__ acc64tt, int last) {
+    corr_kernel(const T* __restrict__ ser, int ns, long long n0, int M, int L, T* __restrict__ hist,
+                T* __restrict__ lev, size_t lev_half, double* __restrict__ acc64, double* __restrict__ acc64tt) {
     __shared__ T red[kSliceChains * 96];
     const int lane = threadIdx.x & 31;
     const int cc = lane / 6, q = lane % 6;
     const int slot = (threadIdx.x >> 5) * kCorrChainsPerWarp + cc;  // chain within the slice
-    const int m = blockIdx.x * kSliceChains + slot;
-    const bool live = lane < 30 && slot < kSliceChains && m < M;
-    const int mm = live ? m : 0;
-    const int src_lane = cc * 6 + q % 3;
-    T* h = hist + (((size_t)mm * L) * 6 + q) * 16;
-    T r[16], acc[16], acc2[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        r[i] = live ? h[i] : T(0);
-        acc[i] = T(0);
-        acc2[i] = T(0);
-    }
-    int nr = 0;
-    const T* yrow = ser + (size_t)mm * 6 + q;
-    const size_t stride = (size_t)M * 6;
-    corr_ring_products<T, 0, TT>(r, acc, acc2, [&](int j) { return yrow[(size_t)j * stride]; }, ns,
-                                 min(src_lane, 31), nr);
-    corr_fold_slice(acc, 0, live, lane < 30 ? slot : kSliceChains, q, acc64 + ((size_t)blockIdx.x * L) * 96, red);
-    if constexpr (TT)
-        corr_fold_slice_tt(acc2, 0, live, lane < 30 ? slot : kSliceChains, q,
-                           acc64tt + ((size_t)blockIdx.x * L) * 48, red);
-    if (!live) return;
-    if (last) {
-        T nh[16];
-        corr_ring_newest(r, nr, nh);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = nh[i];
-    }
-}
-
-// Level l >= 1 from the cprev level-(l-1) samples of this launch, yin
-// [cprev][M][6] (absolute indices pb .. pb + cprev - 1); writes the cl new
-// level-l samples to yout [cl][M][6] (absolute indices nb ..).
-template <typename T, bool TT>
-__global__ void __launch_bounds__(kCorrThreads)
-    corr_level_kernel(const T* __restrict__ yin, int cprev, long long pb, long long nb, int cl, int l, int M,
-                      int L, T* __restrict__ hist, T* __restrict__ yout, double* __restrict__ acc64,
-                      double* __restrict__ acc64tt, int last) {
-    __shared__ T red[kSliceChains * 96];
-    const int lane = threadIdx.x & 31;
-    const int cc = lane / 6, q = lane % 6;
-    const int slot = (threadIdx.x >> 5) * kCorrChainsPerWarp + cc;
+    const int fslot = lane < 30 ? slot : kSliceChains;
     const int m = blockIdx.x * kSliceChains + slot;
     const bool live = lane < 30 && slot < kSliceChains && m < M;
     const int mm = live ? m : 0;
     const int src_lane = min(cc * 6 + q % 3, 31);
     const size_t stride = (size_t)M * 6;
-    // level l-1: its newest sample before this launch, then its history brought up to date
-    T* hp = hist + (((size_t)mm * L + (l - 1)) * 6 + q) * 16;
-    T old[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) old[i] = live ? hp[i] : T(0);
-    const T* yrow = yin + (size_t)mm * 6 + q;
-    if (live) {
+    auto cl_of = [&](int l) { return (int)(((n0 + ns) >> l) - (n0 >> l)); };
+
+    // ---- level 0: the raw samples
+    {
+        T* h = hist + (((size_t)mm * L) * 6 + q) * 16;
+        T r[16], acc[16], acc2[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const int src = cprev - 16 + i;  // position among the new samples
-            hp[i] = src >= 0 ? yrow[(size_t)src * stride] : old[cprev + i];
+            r[i] = live ? h[i] : T(0);
+            acc[i] = T(0);
+            acc2[i] = T(0);
+        }
+        int nr = 0;
+        const T* yrow = ser + (size_t)mm * 6 + q;
+        corr_ring_products<T, 0, TT>(r, acc, acc2, [&](int j) { return yrow[(size_t)j * stride]; }, ns, src_lane,
+                                     nr);
+        corr_fold_slice(acc, 0, live, fslot, q, acc64 + ((size_t)blockIdx.x * L) * 96, red);
+        if constexpr (TT) corr_fold_slice_tt(acc2, 0, live, fslot, q, acc64tt + ((size_t)blockIdx.x * L) * 48, red);
+        if (live && (L == 1 || cl_of(1) == 0)) {  // no level above brings it up to date
+            T nh[16];
+            corr_ring_newest(r, nr, nh);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) h[i] = nh[i];
         }
     }
-    // level l samples: pairs (2J, 2J+1) of level l-1, the first possibly
-    // straddling the launch boundary; stored for level l+1 as they are made
-    const int off = (int)(2 * nb - pb);  // -1 or 0
-    const T pend = old[15];
-    T* orow = yout + (size_t)mm * 6 + q;
-    auto mean = [&](int j) {
-        const int a0 = off + 2 * j;
-        const T v0 = a0 >= 0 ? yrow[(size_t)a0 * stride] : pend;
-        const T v = T(0.5) * (v0 + yrow[(size_t)(a0 + 1) * stride]);
-        if (live) orow[(size_t)j * stride] = v;
-        return v;
-    };
-    // lag products of level l over its new samples
-    T* h = hist + (((size_t)mm * L + l) * 6 + q) * 16;
-    T r[16], acc[16], acc2[16];
+
+    // ---- levels 1..: the cprev samples of level l-1 of this launch, yin
+    // (absolute indices pb ..), give the cl samples of level l (absolute nb ..)
+    const T* yin = ser;
+    int cprev = ns;
+    for (int l = 1; l < L; ++l) {
+        const int cl = cl_of(l);
+        if (cl == 0) break;  // no new sample here or above
+        const long long pb = n0 >> (l - 1), nb = n0 >> l;
+        T* yout = lev + (size_t)((l - 1) & 1) * lev_half;
+        const bool last = (l == L - 1) || cl_of(l + 1) == 0;
+        // level l-1: its newest sample before this launch, then its history brought up to date
+        T* hp = hist + (((size_t)mm * L + (l - 1)) * 6 + q) * 16;
+        T old[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        r[i] = live ? h[i] : T(0);
-        acc[i] = T(0);
-        acc2[i] = T(0);
-    }
-    int nr = 0;
-    corr_ring_products<T, kP / 2, TT>(r, acc, acc2, mean, cl, src_lane, nr);
-    corr_fold_slice(acc, kP / 2, live, lane < 30 ? slot : kSliceChains, q,
-                    acc64 + ((size_t)blockIdx.x * L + l) * 96, red);
-    if constexpr (TT)
-        corr_fold_slice_tt(acc2, kP / 2, live, lane < 30 ? slot : kSliceChains, q,
-                           acc64tt + ((size_t)blockIdx.x * L + l) * 48, red);
-    if (!live) return;
-    if (last) {
-        T nh[16];
-        corr_ring_newest(r, nr, nh);
+        for (int i = 0; i < 16; ++i) old[i] = live ? hp[i] : T(0);
+        const T* yrow = yin + (size_t)mm * 6 + q;
+        if (live) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = nh[i];
+            for (int i = 0; i < 16; ++i) {
+                const int src = cprev - 16 + i;  // position among the new samples
+                hp[i] = src >= 0 ? yrow[(size_t)src * stride] : old[cprev + i];
+            }
+        }
+        // level-l samples: pairs (2J, 2J+1) of level l-1, the first possibly
+        // straddling the launch boundary; stored for level l+1 as they are made
+        const int off = (int)(2 * nb - pb);  // -1 or 0
+        const T pend = old[15];
+        T* orow = yout + (size_t)mm * 6 + q;
+        auto mean = [&](int j) {
+            const int a0 = off + 2 * j;
+            const T v0 = a0 >= 0 ? yrow[(size_t)a0 * stride] : pend;
+            const T v = T(0.5) * (v0 + yrow[(size_t)(a0 + 1) * stride]);
+            if (live) orow[(size_t)j * stride] = v;
+            return v;
+        };
+        T* h = hist + (((size_t)mm * L + l) * 6 + q) * 16;
+        T r[16], acc[16], acc2[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            r[i] = live ? h[i] : T(0);
+            acc[i] = T(0);
+            acc2[i] = T(0);
+        }
+        int nr = 0;
+        corr_ring_products<T, kP / 2, TT>(r, acc, acc2, mean, cl, src_lane, nr);
+        corr_fold_slice(acc, kP / 2, live, fslot, q, acc64 + ((size_t)blockIdx.x * L + l) * 96, red);
+        if constexpr (TT)
+            corr_fold_slice_tt(acc2, kP / 2, live, fslot, q, acc64tt + ((size_t)blockIdx.x * L + l) * 48, red);
+        if (live && last) {
+            T nh[16];
+            corr_ring_newest(r, nr, nh);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) h[i] = nh[i];
+        }
+        yin = yout;
+        cprev = cl;
     }
 }
 
