@@ -229,9 +229,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = _max_over_ranks(time.perf_counter() - te, ws)
     e2e_value = float(M) * N * spc * e2e_steps * ws / e2e_s
-    h2d = M * 3 * 32 * 4 * 2 + M * 32 * 4 + M * 4
-    slices = (M + 63) // 64
-    d2h = slices * w["levels"] * 96 * 8
+    # set_state copies the caller's arrays as they are (R, A double; S, Z int32) and
+    # reads back a 4-byte check flag; correlator() copies the FP64 group sums
+    zm = min(N, 64)
+    h2d = M * (N * 3 * 8 + zm * 3 * 8 + zm * 4 + 4)
+    d2h = 32 * w["levels"] * 96 * 8 + 4
     ge.close()
 
     if rank != 0:

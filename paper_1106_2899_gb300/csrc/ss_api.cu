@@ -75,6 +75,8 @@ struct ss_ctx {
     long long log_m0 = 0;
     unsigned long long* counters = nullptr;  // [8]
     int32_t* status = nullptr;
+    void* stage = nullptr;  // device staging for state uploads and correlator readout
+    size_t stage_bytes = 0;
     long long launches = 0;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // chain-kernel launches while timing
@@ -134,6 +136,20 @@ int fail(ss_ctx* c, int code, const std::string& msg) {
     } while (0)
 
 size_t tsize(const ss_ctx* c) { return c->prec == SS_FP64 ? sizeof(double) : sizeof(float); }
+
+// device staging of at least `bytes`, grown on demand and kept for the context
+int stage_at_least(ss_ctx* c, size_t bytes) {
+    if (c->stage_bytes >= bytes) return SS_OK;
+    if (c->stage) {
+        SS_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->stage);
+        c->stage = nullptr;
+        c->stage_bytes = 0;
+    }
+    SS_CUDA(c, cudaMalloc(&c->stage, bytes));
+    c->stage_bytes = bytes;
+    return SS_OK;
+}
 
 void free_elem(Elem& e) {
     void* ptrs[] = {e.R, e.A, e.S, e.Z, e.hist, e.acc64, e.acc64tt, e.ser, e.lev, e.logs, e.kap_d, e.kfrom_d};
@@ -432,25 +448,6 @@ Elem* elem_at(ss_ctx* c, int e) {
 }
 
 template <typename T>
-void to_device_layout(const Elem& e, const double* R, const int32_t* Z, const int32_t* S, const double* A,
-                      std::vector<T>& Rd, std::vector<T>& Ad, std::vector<int32_t>& Sd, std::vector<int32_t>& Zd) {
-    const int W = e.NP, N = e.N, zm = e.zmax;
-    Rd.assign((size_t)e.M * 3 * W, T(0));
-    Ad.assign((size_t)e.M * 3 * W, T(0));
-    Sd.assign((size_t)e.M * W, -1);
-    Zd.assign((size_t)e.M, 0);
-    for (int m = 0; m < e.M; ++m) {
-        for (int i = 0; i < N; ++i)
-            for (int d = 0; d < 3; ++d) Rd[((size_t)m * 3 + d) * W + i] = T(R[((size_t)m * N + i) * 3 + d]);
-        Zd[m] = Z[m];
-        for (int j = 0; j < Z[m]; ++j) {
-            Sd[(size_t)m * W + j] = S[(size_t)m * zm + j];
-            for (int d = 0; d < 3; ++d) Ad[((size_t)m * 3 + d) * W + j] = T(A[((size_t)m * zm + j) * 3 + d]);
-        }
-    }
-}
-
-template <typename T>
 int get_state_t(ss_ctx* c, Elem& e, double* R, int32_t* Z, int32_t* S, double* A) {
     const int W = e.NP, N = e.N, zm = e.zmax;
     std::vector<T> Rd((size_t)e.M * 3 * W), Ad((size_t)e.M * 3 * W);
@@ -478,18 +475,44 @@ int get_state_t(ss_ctx* c, Elem& e, double* R, int32_t* Z, int32_t* S, double* A
 
 template <typename T>
 int set_state_t(ss_ctx* c, Elem& e, const double* R, const int32_t* Z, const int32_t* S, const double* A) {
-    std::vector<T> Rd, Ad;
-    std::vector<int32_t> Sd, Zd;
-    to_device_layout<T>(e, R, Z, S, A, Rd, Ad, Sd, Zd);
-    SS_CUDA(c, cudaMemcpyAsync(e.R, Rd.data(), Rd.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-    SS_CUDA(c, cudaMemcpyAsync(e.A, Ad.data(), Ad.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-    SS_CUDA(c, cudaMemcpyAsync(e.S, Sd.data(), Sd.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-    SS_CUDA(c, cudaMemcpyAsync(e.Z, Zd.data(), Zd.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    // the caller's arrays go to the device as they are; checked and converted there
+    const size_t M = e.M, N = e.N, zm = e.zmax;
+    const size_t bR = M * N * 3 * sizeof(double), bA = M * zm * 3 * sizeof(double);
+    const size_t bS = M * zm * sizeof(int32_t), bZ = M * sizeof(int32_t);
+    const size_t oA = (bR + 255) & ~(size_t)255, oS = (oA + bA + 255) & ~(size_t)255;
+    const size_t oZ = (oS + bS + 255) & ~(size_t)255, oF = (oZ + bZ + 255) & ~(size_t)255;
+    int rc = stage_at_least(c, oF + sizeof(int));
+    if (rc != SS_OK) return rc;
+    char* st = static_cast<char*>(c->stage);
+    const double* dR = reinterpret_cast<const double*>(st);
+    const double* dA = reinterpret_cast<const double*>(st + oA);
+    const int32_t* dS = reinterpret_cast<const int32_t*>(st + oS);
+    const int32_t* dZ = reinterpret_cast<const int32_t*>(st + oZ);
+    int* dF = reinterpret_cast<int*>(st + oF);
+    SS_CUDA(c, cudaMemcpyAsync(st, R, bR, cudaMemcpyHostToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(st + oA, A, bA, cudaMemcpyHostToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(st + oS, S, bS, cudaMemcpyHostToDevice, c->stream));
+    SS_CUDA(c, cudaMemcpyAsync(st + oZ, Z, bZ, cudaMemcpyHostToDevice, c->stream));
+    SS_CUDA(c, cudaMemsetAsync(dF, 0, sizeof(int), c->stream));
+    const int width = std::max(e.N, e.zmax);
+    const long long nchk = (long long)e.M * width, ncv = (long long)e.M * e.NP;
+    ssk::state_check_kernel<<<(unsigned)((nchk + 255) / 256), 256, 0, c->stream>>>(dR, dA, dS, dZ, e.M, e.N, e.zmax,
+                                                                                  width, dF);
+    SS_CUDA(c, cudaGetLastError());
+    int bad = 0;
+    SS_CUDA(c, cudaMemcpyAsync(&bad, dF, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad & 1) return fail(c, SS_EINVAL, "Z out of range");
+    if (bad & 2) return fail(c, SS_EINVAL, "S out of range");
+    if (bad & 4) return fail(c, SS_EINVAL, "non-finite A");
+    if (bad & 8) return fail(c, SS_EINVAL, "non-finite R");
+    ssk::state_convert_kernel<T><<<(unsigned)((ncv + 255) / 256), 256, 0, c->stream>>>(
+        dR, dA, dS, dZ, e.M, e.N, e.zmax, e.NP, static_cast<T*>(e.R), static_cast<T*>(e.A), e.S, e.Z);
+    SS_CUDA(c, cudaGetLastError());
+    c->launches += 2;
     return SS_OK;
 }
 
-// group sums [G][L][16][2][3] from the per-slice device sums
 // channel TT per group: out[G][L][16][3]
 int group_corr_tt(ss_ctx* c, Elem& e, std::vector<double>& out) {
     const int L = c->levels;
@@ -507,22 +530,18 @@ int group_corr_tt(ss_ctx* c, Elem& e, std::vector<double>& out) {
     return SS_OK;
 }
 
+// group sums [G][L][16][2][3] from the per-slice device sums, summed on the device
 int group_corr(ss_ctx* c, Elem& e, std::vector<double>& out) {
     const int L = c->levels;
-    std::vector<double> sl((size_t)e.slices * L * 96);
-    SS_CUDA(c, cudaMemcpyAsync(sl.data(), e.acc64, sl.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    const size_t n = (size_t)e.groups * L * 96;
+    int rc = stage_at_least(c, n * sizeof(double));
+    if (rc != SS_OK) return rc;
+    double* d = static_cast<double*>(c->stage);
+    ssk::corr_group_kernel<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(e.acc64, e.slices, e.groups, L, d);
+    SS_CUDA(c, cudaGetLastError());
+    out.resize(n);
+    SS_CUDA(c, cudaMemcpyAsync(out.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SS_CUDA(c, cudaStreamSynchronize(c->stream));
-    out.assign((size_t)e.groups * L * 16 * 6, 0.0);
-    for (int s = 0; s < e.slices; ++s) {
-        const int g = (int)(((long long)s * e.groups) / e.slices);
-        for (int l = 0; l < L; ++l)
-            for (int d = 0; d < 3; ++d)
-                for (int cell = 0; cell < 32; ++cell) {
-                    const int ch = cell >> 4, lag = cell & 15;
-                    out[((((size_t)g * L + l) * 16 + lag) * 2 + ch) * 3 + d] +=
-                        sl[((size_t)s * L + l) * 96 + d * 32 + cell];
-                }
-    }
     return SS_OK;
 }
 
@@ -1347,6 +1366,7 @@ int ss_destroy(ss_ctx* c) {
     free_window(c);
     if (c->counters) cudaFree(c->counters);
     if (c->status) cudaFree(c->status);
+    if (c->stage) cudaFree(c->stage);
     delete c;
     return SS_OK;
 }
@@ -1367,17 +1387,6 @@ int ss_set_state(ss_ctx* c, int elem, const double* R, const int32_t* Z, const i
     Elem* e = elem_at(c, elem);
     if (!e || !R || !Z || !S || !A) return fail(c, SS_EINVAL, "bad element or NULL array");
     if (!c->have_params) return fail(c, SS_ESTATE, "ss_set_params must precede ss_set_state");
-    for (int m = 0; m < e->M; ++m) {
-        if (Z[m] < 0 || Z[m] > e->zmax) return fail(c, SS_EINVAL, "Z out of range");
-        for (int j = 0; j < Z[m]; ++j) {
-            const int s = S[(size_t)m * e->zmax + j];
-            if (s < 0 || s >= e->N) return fail(c, SS_EINVAL, "S out of range");
-            for (int d = 0; d < 3; ++d)
-                if (!std::isfinite(A[((size_t)m * e->zmax + j) * 3 + d])) return fail(c, SS_EINVAL, "non-finite A");
-        }
-        for (int i = 0; i < e->N * 3; ++i)
-            if (!std::isfinite(R[(size_t)m * e->N * 3 + i])) return fail(c, SS_EINVAL, "non-finite R");
-    }
     int rc = c->prec == SS_FP64 ? set_state_t<double>(c, *e, R, Z, S, A) : set_state_t<float>(c, *e, R, Z, S, A);
     if (rc != SS_OK) return rc;
     // every element must hold a state before stepping: sample the others once

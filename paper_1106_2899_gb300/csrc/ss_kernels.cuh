@@ -1224,6 +1224,66 @@ __global__ void __launch_bounds__(kCorrThreads)
     }
 }
 
+// ------------------------------------------------------- state upload ------
+// A caller's state in the host layout (R [M][N][3], A [M][zm][3] double;
+// S [M][zm], Z [M] int32), staged on the device as it is, checked and then
+// converted to the device layout.  One thread per (chain, bead or slot i).
+// bad: bit 1 Z out of 0..zm, 2 S out of 0..N-1, 4 A not finite, 8 R not finite.
+__global__ void state_check_kernel(const double* __restrict__ R, const double* __restrict__ A,
+                                   const int32_t* __restrict__ S, const int32_t* __restrict__ Z, int M, int N,
+                                   int zm, int width, int* __restrict__ bad) {
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)M * width) return;
+    const int m = (int)(id / width), i = (int)(id % width);
+    const int z = Z[m];
+    int f = 0;
+    if (i == 0 && (z < 0 || z > zm)) f |= 1;
+    if (i < N)
+        for (int d = 0; d < 3; ++d)
+            if (!isfinite(R[((size_t)m * N + i) * 3 + d])) f |= 8;
+    if (i < zm && i < z) {
+        const int sj = S[(size_t)m * zm + i];
+        if (sj < 0 || sj >= N) f |= 2;
+        for (int d = 0; d < 3; ++d)
+            if (!isfinite(A[((size_t)m * zm + i) * 3 + d])) f |= 4;
+    }
+    if (f) atomicOr(bad, f);
+}
+
+template <typename T>
+__global__ void state_convert_kernel(const double* __restrict__ Rh, const double* __restrict__ Ah,
+                                     const int32_t* __restrict__ Sh, const int32_t* __restrict__ Zh, int M, int N,
+                                     int zm, int NP, T* __restrict__ R, T* __restrict__ A, int32_t* __restrict__ S,
+                                     int32_t* __restrict__ Z) {
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)M * NP) return;
+    const int m = (int)(id / NP), i = (int)(id % NP);
+    const int z = Zh[m];
+    if (i == 0) Z[m] = z;
+    for (int d = 0; d < 3; ++d) {
+        R[((size_t)m * 3 + d) * NP + i] = i < N ? T(Rh[((size_t)m * N + i) * 3 + d]) : T(0);
+        A[((size_t)m * 3 + d) * NP + i] = i < z ? T(Ah[((size_t)m * zm + i) * 3 + d]) : T(0);
+    }
+    S[(size_t)m * NP + i] = i < z ? Sh[(size_t)m * zm + i] : -1;
+}
+
+// Correlator group sums from the slice sums: out[g][l][lag][ch][d] (the layout
+// of ss_corr_sums) = sum over the slices of group g, in slice order, of
+// acc64[s][l][d * 32 + ch * 16 + lag].  One thread per (g, l, cell).
+__global__ void corr_group_kernel(const double* __restrict__ acc64, int slices, int groups, int L,
+                                  double* __restrict__ out) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= groups * L * 96) return;
+    const int g = id / (L * 96), l = (id / 96) % L, i = id % 96;
+    const int d = i / 32, ch = (i % 32) / 16, lag = i % 16;
+    // slices of group g: s with floor(s * groups / slices) == g
+    const int s0 = (int)(((long long)g * slices + groups - 1) / groups);
+    const int s1 = (int)(((long long)(g + 1) * slices + groups - 1) / groups);
+    double sum = 0.0;
+    for (int sl = s0; sl < s1; ++sl) sum += acc64[((size_t)sl * L + l) * 96 + i];
+    out[((((size_t)g * L + l) * 16 + lag) * 2 + ch) * 3 + d] = sum;
+}
+
 // ------------------------------------------------------------ init kernel ----
 // Equilibrium initial state (Sec. 3.1 sampling): ideal-chain bonds with
 // variance kT/k_b per component, Z ~ Poisson(N/N0) by inverse CDF on a 53-bit
