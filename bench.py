@@ -216,7 +216,13 @@ def run_ours(args):
     # ---------------- end to end through the C ABI with host buffers
     ge = make(args.chunk)
     ge.run(0)
-    host_state = ge.get_state()
+    # the step's inputs live in pinned host memory (numpy views of pinned tensors)
+    host_state = {}
+    for k, v in ge.get_state().items():
+        pinned = torch.empty(v.shape, dtype=torch.float64 if v.dtype == np.float64 else torch.int32,
+                             pin_memory=True).numpy()
+        pinned[...] = v
+        host_state[k] = pinned
     ge.run(spc)
     ge.correlator("total")
     torch.cuda.synchronize()
