@@ -227,11 +227,14 @@ int ss_log_sums(ss_ctx* ctx, int elem, int64_t* log_step, double* sums, int cap,
 /* Event counters summed over all chains since ss_set_params: out[0] hops to
  * S+1, out[1] hops to S-1, out[2] springs created, out[3] springs destroyed,
  * out[4] creation attempts dropped at capacity (K = 1 form), out[5] kernel
- * launches, out[6] non-finite-state detections. */
-int ss_counters(ss_ctx* ctx, int64_t out[7]);
+ * launches, out[6] non-finite-state detections, out[7] broken-invariant
+ * detections (see ss_status). */
+int ss_counters(ss_ctx* ctx, int64_t out[8]);
 
-/* Device status word: 0 if every step so far kept a finite state; bit 0 set
- * if a non-finite bead position was found.  Synchronises. */
+/* Device status word, checked by every chain-kernel launch on the state it
+ * leaves: 0 if all is well; bit 0 set if a bead position was not finite, bit 1
+ * if a chain broke 0 <= Z <= z_max or 0 <= S_j < N (a defect of the step, not
+ * of the model).  Synchronises. */
 int ss_status(ss_ctx* ctx, int32_t* status);
 
 /* Wait for the context's stream. */

@@ -209,10 +209,10 @@ class SlipSpring:
         return t, L
 
     def counters(self):
-        out = np.zeros(7, dtype=np.int64)
+        out = np.zeros(8, dtype=np.int64)
         self._chk(self.lib.ss_counters(self.h, _p(out, C.c_int64)), "ss_counters")
         return dict(zip(["hops_up", "hops_down", "created", "destroyed", "dropped", "launches",
-                         "nonfinite"], out.tolist()))
+                         "nonfinite", "broken"], out.tolist()))
 
     def kernel_timing(self, enable=True):
         """Bracket each chain-kernel launch with CUDA events (benchmark support)."""

@@ -5,6 +5,7 @@
 // chunk of chunk_steps steps, one launch of the chain kernel per element.
 // Parameters are validated here, on the host; kernels assume valid input.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <array>
@@ -137,6 +138,14 @@ int fail(ss_ctx* c, int code, const std::string& msg) {
 
 size_t tsize(const ss_ctx* c) { return c->prec == SS_FP64 ? sizeof(double) : sizeof(float); }
 
+// NVTX range for profilers (a no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // device staging of at least `bytes`, grown on demand and kept for the context
 int stage_at_least(ss_ctx* c, size_t bytes) {
     if (c->stage_bytes >= bytes) return SS_OK;
@@ -263,6 +272,7 @@ int corr_launches(const T* ser, int ns, int M, int L, long long n0, T* hist, dou
 
 template <typename T, int W, int B>
 int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
+    NvtxRange range("chain kernel + correlator launch");
     const ss_params& p = c->P;
     ssk::ChunkArgs a{};
     a.R = e.R;
@@ -1227,6 +1237,7 @@ int ss_set_batched(ss_ctx* c, int enable) {
 
 int ss_run(ss_ctx* c, int64_t n_steps) {
     if (!c) return SS_EINVAL;
+    NvtxRange range("ss_run");
     if (!c->have_params) return fail(c, SS_ESTATE, "ss_set_params must precede ss_run");
     if (n_steps < 0) return fail(c, SS_EINVAL, "n_steps must be >= 0");
     if (c->step + n_steps > 0xFFFFFFFFll) return fail(c, SS_EOVERFLOW, "step counter would pass 2^32");
@@ -1480,7 +1491,7 @@ int ss_log_sums(ss_ctx* c, int elem, int64_t* log_step, double* sums, int cap, i
     return SS_OK;
 }
 
-int ss_counters(ss_ctx* c, int64_t out[7]) {
+int ss_counters(ss_ctx* c, int64_t out[8]) {
     if (!c || !out) return SS_EINVAL;
     unsigned long long h[8] = {0};
     SS_CUDA(c, cudaMemcpyAsync(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -1488,6 +1499,7 @@ int ss_counters(ss_ctx* c, int64_t out[7]) {
     for (int i = 0; i < 5; ++i) out[i] = (int64_t)h[i];
     out[5] = c->launches;
     out[6] = (int64_t)h[6];
+    out[7] = (int64_t)h[7];
     return SS_OK;
 }
 
@@ -1532,6 +1544,7 @@ int ss_kernel_time(ss_ctx* c, double* chain_kernel_ms, int64_t* chain_launches) 
 
 int ss_window_forward(ss_ctx* c, int64_t n_steps, int checkpoint_every, int replay) {
     if (!c) return SS_EINVAL;
+    NvtxRange range("ss_window_forward");
     if (!c->have_params) return fail(c, SS_ESTATE, "ss_set_params must precede a window");
     if (c->el.size() != 1) return fail(c, SS_EINVAL, "a differentiation window needs exactly one element");
     if (c->levels <= 0) return fail(c, SS_EINVAL, "a differentiation window needs the correlator (corr_levels > 0)");
@@ -1626,6 +1639,7 @@ int ss_set_coefficients(ss_ctx* c, double k_b, double k_s, double zeta) {
 int ss_window_backward(ss_ctx* c, const double* dL_dG, double grad[3]) {
     if (!c || !dL_dG || !grad) return SS_EINVAL;
     if (!c->win.forward_done) return fail(c, SS_ESTATE, "ss_window_forward must precede ss_window_backward");
+    NvtxRange range("ss_window_backward");
     return c->prec == SS_FP64 ? window_backward_t<double>(c, dL_dG, grad) : window_backward_t<float>(c, dL_dG, grad);
 }
 }  // extern "C"

@@ -196,7 +196,7 @@ struct ChunkArgs {
     int32_t* S;         // [M][W]
     int32_t* Z;         // [M]
     double* logs;       // [max_logs][groups][14]
-    unsigned long long* counters;  // [8]
+    unsigned long long* counters;  // [8]: events 0..4, 6 non-finite states, 7 broken invariants
     int32_t* status;
     const double* kap;          // [n_kap][9]
     const long long* kap_from;  // [n_kap]
@@ -898,13 +898,15 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     // ---- store state
     T* Rw = static_cast<T*>(a.R);
     T* Aw = static_cast<T*>(a.A);
-    bool bad = false;
+    bool bad = false, broken = false;  // non-finite position; broken invariant 0 <= Z <= z_max, 0 <= S < N
     if (live) {
         if (ll == 0) a.Z[mm] = Z;
+        broken = Z < 0 || Z > a.zmax;
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
             a.S[(size_t)mm * NP + i] = (i < Z) ? S[b] : -1;
+            broken |= (i < Z) && (S[b] < 0 || S[b] >= N);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (i < N) {
@@ -918,6 +920,10 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     if (__any_sync(kFull, bad) && lane == 0) {
         atomicOr(a.status, 1);
         atomicAdd(a.counters + 6, 1ull);
+    }
+    if (__any_sync(kFull, broken) && lane == 0) {
+        atomicOr(a.status, 2);
+        atomicAdd(a.counters + 7, 1ull);
     }
 
     // ---- event counters (padding segments beyond the element's chains count nothing)

@@ -343,3 +343,53 @@ def test_error_paths():
         g.set_flow(np.full(9, np.nan))
     g.run(20)
     assert g.status() == 0
+
+
+# ------------------------------------------------- resume, failure detection --
+def test_resume_from_saved_state_is_bit_exact():
+    """Checkpoint/resume: the state after 300 steps, loaded into a new context
+    with the step counter set to 300, continues bit for bit like one 600-step
+    run (counter-based random numbers), with and without flow (recentring
+    happens at absolute steps)."""
+    for kappa in (None, synth.shear_kappa(0.05)):
+        p = Params(N=24)
+        ref = _gpu_ctx(p, 100, 7, "fp32", levels=-1)
+        if kappa is not None:
+            ref.set_flow(kappa, 0)
+        ref.run(600)
+        a = _gpu_ctx(p, 100, 7, "fp32", levels=-1)
+        if kappa is not None:
+            a.set_flow(kappa, 0)
+        a.run(300)
+        saved = a.get_state()
+        b = _gpu_ctx(p, 100, 7, "fp32", levels=-1)
+        if kappa is not None:
+            b.set_flow(kappa, 0)
+        b.set_state(saved)
+        b.step = 300
+        b.run(300)
+        s_ref, s_b = ref.get_state(), b.get_state()
+        for k in ("R", "A", "Z", "S"):
+            assert np.array_equal(s_ref[k], s_b[k]), (k, kappa is not None)
+
+
+def test_nonfinite_state_is_reported_not_faulted():
+    """Failure detection on the device: a chain driven to overflow (bond forces
+    beyond FP32 range) sets status bit 0 and the non-finite counter; the other
+    chains, the integer state and the invariant bit are unaffected."""
+    g = SlipSpring([(40, 16)], precision="fp32", seed=3)
+    g.set_params(**synth.PAPER, corr_levels=8, groups=4)
+    g.run(10)
+    st = g.get_state()
+    st["R"][5, ::2] += 3.0e38  # finite in FP32, but the next bond forces overflow
+    g.set_state(st)
+    g.run(5)
+    s = g.status()
+    c = g.counters()
+    assert s & 1 and c["nonfinite"] >= 1
+    assert not (s & 2) and c["broken"] == 0
+    out = g.get_state()
+    ok = np.ones(40, bool)
+    ok[5] = False
+    assert np.all(np.isfinite(out["R"][ok]))
+    assert np.all((out["Z"] >= 0) & (out["Z"] <= 16))
