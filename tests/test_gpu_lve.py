@@ -6,12 +6,18 @@ plateau of the linear-viscoelastic data of equilibrium runs up to N = 80.
 Here the plateau of the TOTAL-channel G(t) at N = 80 (the value where ln G is
 flattest in ln t) is checked against that printed value as a +-30% sanity
 band (printed numbers of the paper are qualitative).
+
+Entangled scaling: for large N the paper finds tau_d ~ (N - 1)^3.48 (tau_d
+from the tail of ln G, 1/tau_d = -lim ln G(t)/t) and eta0 ~ (N - 1)^3.40
+(eta0 = integral of G).  The exponents between N = 40 and N = 80, from
+equilibrium runs long enough for G(t) to decay by three decades, are checked
+within +-0.3.
 """
 import numpy as np
 import pytest
 
 import synth
-from paper_1106_2899_gb300 import SlipSpring
+from paper_1106_2899_gb300 import SlipSpring, rheology
 
 pytestmark = pytest.mark.gpu
 
@@ -50,3 +56,32 @@ def test_plateau_modulus_at_N80():
     print("\nN=80: plateau G = %.4f rho0 kT (log-slope %.3f); N_e = %.1f" % (GN, slopes[i], 1.0 / GN))
     assert slopes[i] < 0.2  # a plateau region exists
     assert 0.07 <= GN <= 0.13, GN
+
+
+def _eta0_tau_d(N, M, steps):
+    g = SlipSpring([(M, N)], precision="fp32", seed=N + 1)
+    g.set_params(**synth.PAPER, corr_levels=24, groups=32)
+    g.run(20000)
+    g.reset_observables()
+    g.run(steps)
+    assert g.status() == 0
+    t, G, se = g.correlator("total")
+    o = np.argsort(t)
+    t, G, se = t[o], G[o], se[o]
+    ok = (se < 0.3 * np.abs(G)) | (t < 1)  # lags resolved to 30%
+    eta0 = rheology.zero_shear_viscosity(t[ok], G[ok])
+    tr = t[ok & (G > 0)]
+    tau_d = rheology.longest_relaxation_time(t[ok], G[ok], t_min=tr.max() / 10)  # the last resolved decade
+    return eta0, tau_d
+
+
+@pytest.mark.slow
+def test_entangled_scaling_exponents_between_N40_and_N80():
+    e40, t40 = _eta0_tau_d(40, 16384, 1500000)
+    e80, t80 = _eta0_tau_d(80, 4096, 5000000)
+    r = np.log(79.0 / 39.0)
+    a_eta, a_tau = np.log(e80 / e40) / r, np.log(t80 / t40) / r
+    print("\neta0 %.4g -> %.4g, tau_d %.4g -> %.4g: exponents eta0 %.2f (paper 3.40), tau_d %.2f (paper 3.48)"
+          % (e40, e80, t40, t80, a_eta, a_tau))
+    assert abs(a_eta - 3.40) <= 0.3, a_eta
+    assert abs(a_tau - 3.48) <= 0.3, a_tau
