@@ -297,7 +297,7 @@ int ss_window_backward(ss_ctx* ctx, const double* dL_dG, double grad[3]);
  * It calls no cudaMalloc, cudaFree or allocating library routine.
  *
  * State (device pointers, read and written in place), with NP = n_beads
- * rounded up to a multiple of 16:
+ * rounded up to a multiple of 16 for n_beads <= 64, and NP = 128 above:
  *   R [n_chains][3][NP], A [n_chains][3][NP] (float for SS_FP32, double for
  *   SS_FP64; entries beyond n_beads / beyond Z are ignored), S [n_chains][NP]
  *   int32 bead index of slot j (j < Z), Z [n_chains] int32.

@@ -112,7 +112,7 @@ def test_backward_restores_final_state_and_zero_loss_gives_zero_gradient():
         assert np.array_equal(s0[k], s1[k]), k
 
 
-@pytest.mark.parametrize("N,ce", [(24, 256), (16, 100), (40, 128)])
+@pytest.mark.parametrize("N,ce", [(24, 256), (16, 100), (40, 128), (80, 128)])
 def test_fp64_adjoint_matches_replayed_finite_differences(N, ce):
     M, levels = 256, 8
     g = _ctx(M, N, "fp64", levels, seed=7, burn=300)

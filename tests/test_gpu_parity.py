@@ -64,9 +64,9 @@ def _compare_states(go, oo, ok, rtol, what):
 
 
 # --------------------------------------------------------------- init -----
-@pytest.mark.parametrize("precision,N", [("fp64", 16), ("fp32", 32), ("fp32", 11)])
+@pytest.mark.parametrize("precision,N", [("fp64", 16), ("fp32", 32), ("fp32", 11), ("fp64", 100)])
 def test_equilibrium_init_matches_oracle(precision, N):
-    p = Params(N=N)
+    p = Params(N=N, z_max=min(N, 64))
     M = 300
     g = _gpu_ctx(p, M, seed=5, precision=precision)
     g.run(0)
@@ -218,9 +218,9 @@ def _first_tie(margins):
     return first
 
 
-@pytest.mark.parametrize("N,kappa", [(32, None), (16, None), (24, 0.05), (48, None)])
+@pytest.mark.parametrize("N,kappa", [(32, None), (16, None), (24, 0.05), (48, None), (80, 0.02)])
 def test_fp32_stepwise_parity_until_near_tie(N, kappa):
-    p = Params(N=N)
+    p = Params(N=N, z_max=min(N, 64))
     M = 512 if N > 16 else 1024
     steps = 600
     g = _gpu_ctx(p, M, 1, "fp32")

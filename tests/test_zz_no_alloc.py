@@ -23,7 +23,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _lanes(N):
-    return 16 if N <= 16 else 32
+    """NP, the padded bead/slot count of the device layout."""
+    return -(-N // 16) * 16 if N <= 64 else 128
 
 
 def _to_device_layout(st, N, zm, dtype):
@@ -59,7 +60,7 @@ def _noalloc_call(lib, params, precision, seed, M, N, t0, n, dev, corr, status, 
     assert rc == 0, nat.ERRORS.get(rc, rc)
 
 
-@pytest.mark.parametrize("precision,N", [("fp64", 16), ("fp32", 32)])
+@pytest.mark.parametrize("precision,N", [("fp64", 16), ("fp32", 32), ("fp32", 80)])
 def test_noalloc_two_calls_match_context(cuda_ok, precision, N):
     import torch
 
@@ -67,7 +68,7 @@ def test_noalloc_two_calls_match_context(cuda_ok, precision, N):
     build.build()
     lib = nat.load()
     M, seed, levels, n1, n2 = 200, 11, 10, 300, 500
-    zm = N
+    zm = min(N, 64)
     st0 = synth.random_state(M, N, zm, seed=3, z_mean=N / 4)
     kw = dict(corr_levels=levels, groups=4, chunk_steps=128)
     prec = nat.SS_FP64 if precision == "fp64" else nat.SS_FP32
