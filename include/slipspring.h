@@ -167,7 +167,11 @@ int ss_stress(ss_ctx* ctx, int elem, double* t, double* mean, double* sem, int c
 /* Relaxation modulus of element elem from the multiple-tau correlator, channel
  * SS_CH_*: t[n] the lag (steps * dt), G[n] in rho0 kT averaged over the xy, xz,
  * yz components, sem[n] its standard error over chain groups.  Lags are
- * ascending; lags without samples are left out.  *n_out = number available. */
+ * ascending; lags without samples are left out.  *n_out = number available.
+ * Writes at most cap entries (any of t, G, sem may be NULL); with cap = 0 or
+ * all three NULL it only sets *n_out and reads nothing from the device.
+ * Otherwise the group sums are reduced on the device and copied back once:
+ * synchronises with the context's stream. */
 int ss_correlator(ss_ctx* ctx, int elem, int channel, double* t, double* G, double* sem, int cap,
                   int* n_out);
 

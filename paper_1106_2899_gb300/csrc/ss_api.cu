@@ -555,11 +555,11 @@ int group_corr(ss_ctx* c, Elem& e, std::vector<double>& out) {
     return SS_OK;
 }
 
-int chains_in_group(const Elem& e, int g) {
+// chains of each group (slices are dealt to groups in contiguous runs), one pass over the slices
+std::vector<int> group_sizes(const Elem& e) {
     const int sc = ssk::kSliceChains;
-    int n = 0;
-    for (int s = 0; s < e.slices; ++s)
-        if ((int)(((long long)s * e.groups) / e.slices) == g) n += std::min(sc, e.M - s * sc);
+    std::vector<int> n(e.groups, 0);
+    for (int s = 0; s < e.slices; ++s) n[(int)(((long long)s * e.groups) / e.slices)] += std::min(sc, e.M - s * sc);
     return n;
 }
 
@@ -1284,6 +1284,7 @@ int ss_stress(ss_ctx* c, int elem, double* t, double* mean, double* sem, int cap
     const int n = p.log_every > 0 ? (int)std::min<long long>(c->step / p.log_every - c->log_m0, p.max_logs) : 0;
     if (n_out) *n_out = n;
     if (n == 0 || cap == 0) return SS_OK;
+    const std::vector<int> gsz = group_sizes(*e);
     std::vector<double> L((size_t)n * e->groups * 14);
     SS_CUDA(c, cudaMemcpyAsync(L.data(), e->logs, L.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1294,7 +1295,7 @@ int ss_stress(ss_ctx* c, int elem, double* t, double* mean, double* sem, int cap
             for (int g = 0; g < e->groups; ++g) {
                 const double sg = L[((size_t)i * e->groups + g) * 14 + k];
                 tot += sg;
-                const double mg = sg / chains_in_group(*e, g);
+                const double mg = sg / gsz[g];
                 gm += mg;
                 gm2 += mg * mg;
             }
@@ -1316,6 +1317,12 @@ int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double
     if (!c->have_params || c->levels <= 0) return fail(c, SS_ESTATE, "correlator not enabled");
     const bool tt = channel == SS_CH_TT || channel == SS_CH_VIRTUAL;
     if (tt && !e->acc64tt) return fail(c, SS_ESTATE, "channel TT needs corr_tt = 1");
+    const int L = c->levels, NG = e->groups;
+    int n_slots = 0;  // lags with at least one product: level 0 lags 0..15, level l >= 1 lags 8..15
+    for (int l = 0; l < L; ++l)
+        for (int k = (l == 0 ? 0 : 8); k < 16; ++k) n_slots += (c->nsamp >> l) - k > 0;
+    if (n_out) *n_out = n_slots;
+    if (cap == 0 || (!t && !G && !sem)) return SS_OK;  // a size query reads nothing from the device
     std::vector<double> acc, acc_tt;
     int rc = group_corr(c, *e, acc);
     if (rc != SS_OK) return rc;
@@ -1323,7 +1330,7 @@ int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double
         rc = group_corr_tt(c, *e, acc_tt);
         if (rc != SS_OK) return rc;
     }
-    const int L = c->levels, NG = e->groups;
+    const std::vector<int> gsz = group_sizes(*e);
     const double norm = (double)e->N * c->P.kT * c->P.kT;
     int n = 0;
     for (int l = 0; l < L; ++l)
@@ -1347,7 +1354,7 @@ int ss_correlator(ss_ctx* c, int elem, int channel, double* t, double* G, double
                 }
                 v /= 3.0;
                 tot += v;
-                const double mg = v / ((double)cnt * chains_in_group(*e, g) * norm);
+                const double mg = v / ((double)cnt * gsz[g] * norm);
                 gm += mg;
                 gm2 += mg * mg;
             }
