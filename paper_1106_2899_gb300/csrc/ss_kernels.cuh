@@ -477,25 +477,28 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 
     unsigned cnt_up = 0, cnt_dn = 0, cnt_cr = 0, cnt_de = 0, cnt_drop = 0;
 
-    // slot table: anchors (and bead indices) of the slots; kept current by the
-    // re-indexing below, and rewritten every step only while a flow moves anchors
-    auto write_tab = [&]() {
+    // slot table: the spring vector d_j = R_{S_j} - A_j of every occupied slot
+    // j, written at the end of each step for the next step's spring forces
+    // (d_j does not change when a chain and its anchors are shifted together,
+    // so recentring leaves it valid); the re-indexing below also uses it as
+    // scratch.  Record NP is zero: an empty slot mask reads it.
+    __syncwarp();  // positions of this warp's chains are in the table
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const int i = ll + b * W;
+    for (int b = 0; b < B; ++b) {
+        const int i = ll + b * W;
+        if (i < Z) {
+            const Pos<T> ps = pos[S[b]];
             SlotRec<T> rec;
-            rec.x = A[b][0];
-            rec.y = A[b][1];
-            rec.z = A[b][2];
-            rec.s = i < Z ? S[b] : -1;
+            rec.x = ps.x - A[b][0];
+            rec.y = ps.y - A[b][1];
+            rec.z = ps.z - A[b][2];
+            rec.s = S[b];
             tab[i] = rec;
         }
-    };
-    write_tab();
+    }
     PhiloxPre ppre[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) ppre[b] = philox_pre((uint32_t)(ll + b * W), kPurposeStep, chain_id, c.rk0, c.rk1);
-    bool tab_dirty = false;  // anchors moved (flow, recentring) since the table was written
     if (ll == 0) {
         SlotRec<T> zero;
         zero.x = zero.y = zero.z = T(0);
@@ -525,11 +528,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 #pragma unroll
         for (int b = 0; b < B; ++b)
             tb[b] = (tmode == 2 && tape_row) ? a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] : (uint8_t)0;
-        // ---- slot table and per-bead slot masks for this step's spring forces
-        if (tab_dirty) {
-            write_tab();
-            tab_dirty = false;
-        }
+        // ---- per-bead slot masks for this step's spring forces
 #pragma unroll
         for (int b = 0; b < B; ++b) msk[ll + b * W] = Mask(0);
         // ---- random numbers of this step: block (i, t, STEP, chain) per bead/slot i
@@ -566,43 +565,39 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         Mask mrest[B];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            // springs on this bead: k_s (sum_j A_j - n R), slots in ascending order
+            // springs on this bead: -k_s sum_j d_j, slots in ascending order
             // (an empty mask reads the zero record at NP)
             const Mask m0 = msk[ll + b * W];
             const Mask m1 = m0 & (m0 - Mask(1));
             const int j0 = m0 ? mask_ffs(m0) - 1 : NP;
             const int j1 = m1 ? mask_ffs(m1) - 1 : NP;
             const SlotRec<T> r0 = tab[j0], r1 = tab[j1];
-            const T sx = r0.x + r1.x, sy = r0.y + r1.y, sz = r0.z + r1.z;
-            const T cnt = T((m0 != Mask(0)) + (m1 != Mask(0)));
             const Mask mb = m1 & (m1 - Mask(1));
             mrest[b] = mb;
             more |= mb != Mask(0);
-            F[b][0] += c.k_s * (sx - cnt * R[b][0]);
-            F[b][1] += c.k_s * (sy - cnt * R[b][1]);
-            F[b][2] += c.k_s * (sz - cnt * R[b][2]);
+            F[b][0] -= c.k_s * (r0.x + r1.x);
+            F[b][1] -= c.k_s * (r0.y + r1.y);
+            F[b][2] -= c.k_s * (r0.z + r1.z);
         }
         if (__any_sync(kFull, more)) {  // a third spring on one bead: rare
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 // the first two slots were added already; add the rest in order
                 Mask mb = mrest[b];
-                T sx = T(0), sy = T(0), sz = T(0), cnt = T(0);
+                T sx = T(0), sy = T(0), sz = T(0);
                 while (mb) {
                     const SlotRec<T> r = tab[mask_ffs(mb) - 1];
                     mb &= mb - Mask(1);
                     sx += r.x;
                     sy += r.y;
                     sz += r.z;
-                    cnt += T(1);
                 }
-                F[b][0] += c.k_s * (sx - cnt * R[b][0]);
-                F[b][1] += c.k_s * (sy - cnt * R[b][1]);
-                F[b][2] += c.k_s * (sz - cnt * R[b][2]);
+                F[b][0] -= c.k_s * sx;
+                F[b][1] -= c.k_s * sy;
+                F[b][2] -= c.k_s * sz;
             }
         }
         T Rn[B][3];
-        if (kap_nz) tab_dirty = true;
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
@@ -801,6 +796,31 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 #pragma unroll
             for (int d = 0; d < 3; ++d) R[b][d] = Rn[b][d];
 
+        // ---- spring vectors of the new state, d_j = R_{S_j} - A_j (0 for an
+        // empty slot): next step's spring forces and this step's stress;
+        // sub-slots above every chain's Z in this warp hold none
+        const int zn = (int)__reduce_max_sync(kFull, (unsigned)Z);
+        T dd[B][3];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            dd[b][0] = dd[b][1] = dd[b][2] = T(0);
+            if (b * W < zn) {
+                const int i = ll + b * W;
+                const Pos<T> ps = pos[i < Z ? S[b] : 0];
+                if (i < Z) {
+                    dd[b][0] = ps.x - A[b][0];
+                    dd[b][1] = ps.y - A[b][1];
+                    dd[b][2] = ps.z - A[b][2];
+                    SlotRec<T> rec;
+                    rec.x = dd[b][0];
+                    rec.y = dd[b][1];
+                    rec.z = dd[b][2];
+                    rec.s = S[b];
+                    tab[i] = rec;
+                }
+            }
+        }
+
         // ---- stress of the new state (Eq. stress_tensor_single_chain, App. B)
         const bool do_log = (s == next_log);
         if (do_log) next_log += a.log_every;
@@ -814,19 +834,18 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             for (int b = 0; b < B; ++b) {
                 const int i = ll + b * W;
                 const Pos<T> p1 = pos[i < N - 1 ? i + 1 : i];
-                const Pos<T> ps = pos[i < Z ? S[b] : 0];
-                // the last bead reads itself (q = 0); an empty slot has weight 0
+                // the last bead reads itself (q = 0)
                 const T q[3] = {p1.x - R[b][0], p1.y - R[b][1], p1.z - R[b][2]};
-                const T dd[3] = {ps.x - A[b][0], ps.y - A[b][1], ps.z - A[b][2]};
-                const T ws = i < Z ? c.k_s : T(0);
                 const T kq0 = c.k_b * q[0], kq1 = c.k_b * q[1];
-                const T kd0 = ws * dd[0], kd1 = ws * dd[1];
                 v[0] += kq0 * q[1];
                 v[1] += kq0 * q[2];
                 v[2] += kq1 * q[2];
-                v[3] += kd0 * dd[1];
-                v[4] += kd0 * dd[2];
-                v[5] += kd1 * dd[2];
+                if (b * W < zn) {  // springs (an empty slot's d is 0)
+                    const T kd0 = c.k_s * dd[b][0], kd1 = c.k_s * dd[b][1];
+                    v[3] += kd0 * dd[b][1];
+                    v[4] += kd0 * dd[b][2];
+                    v[5] += kd1 * dd[b][2];
+                }
                 if (do_log) {
                     dgp[0] += kq0 * q[0];
                     dgp[1] += kq1 * q[1];
@@ -869,7 +888,6 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             T com[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) com[d] = seg_sum<T, W>(csum[d]) / T(N);
-            tab_dirty = true;
             __syncwarp();
 #pragma unroll
             for (int b = 0; b < B; ++b) {
