@@ -1085,15 +1085,15 @@ __device__ __forceinline__ void corr_fold_slice(const T (&acc)[16], int k0, bool
 
 // Ring of the newest 16 samples of one row: r[i] holds sample base + i - 16
 // when the next sample to enter is sample base (i.e. after a whole number of
-// 16-sample blocks).  Products of n new samples y (with later values x).
-// Products of n new samples, sample j given by get(j) (a load, or a pair mean
-// that is also stored for the next level); nr returns the ring position of
-// the next sample (the number of samples in the last partial block).
-// With TT, acc2 also takes the row's own sample as the later value (for the
-// rows of sigma + sigma^(v): channel TT).
-template <typename T, int K0, bool TT, typename Get>
-__device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], T (&acc2)[16], Get get, int n,
-                                                   int src_lane, int& nr) {
+// 16-sample blocks).  Products of n new samples, sample j given by get(j) (a
+// load), each later value x taken from lane src_lane; emit(j, y) sees every
+// sample in order (the pair means of the level above are formed there).  nr
+// returns the ring position of the next sample (the number of samples in the
+// last partial block).  With TT, acc2 also takes the row's own sample as the
+// later value (for the rows of sigma + sigma^(v): channel TT).
+template <typename T, int K0, bool TT, typename Get, typename Emit>
+__device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], T (&acc2)[16], Get get, Emit emit,
+                                                   int n, int src_lane, int& nr) {
     int j = 0;
     for (; j + 16 <= n; j += 16) {
         T yv[16];
@@ -1101,6 +1101,7 @@ __device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], T (
         for (int u = 0; u < 16; ++u) yv[u] = get(j + u);  // independent loads first
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
+            emit(j + u, yv[u]);
             const T xv = __shfl_sync(kFull, yv[u], src_lane);
             r[u] = yv[u];
 #pragma unroll
@@ -1116,6 +1117,7 @@ __device__ __forceinline__ void corr_ring_products(T (&r)[16], T (&acc)[16], T (
     for (int u = 0; u < 16; ++u) {
         if (u < rem) {
             const T yv = get(j + u);
+            emit(j + u, yv);
             const T xv = __shfl_sync(kFull, yv, src_lane);
             r[u] = yv;
 #pragma unroll
@@ -1143,14 +1145,17 @@ __device__ __forceinline__ void corr_ring_newest(const T (&r)[16], int nr, T* ou
     }
 }
 
-// All levels of one launch in one kernel: level 0 on the launch's series
-// (ns rows of [M][6]), then each higher level that completes a sample, its
-// samples formed as pairwise means of the level below while they are read and
-// stored for the next level in the ping-pong buffers lev (lev_half elements
-// each).  Every thread reads only rows it wrote itself (its chain and series
-// row); the block synchronises only for the slice folds.
+// All levels of one launch in one kernel.  Level l's pass reads the level-l
+// samples of this launch (the series rows for level 0, else the samples the
+// pass below stored), adds their products, and, as the samples stream by,
+// stores the pairwise means that are the level-(l+1) samples into one of the
+// ping-pong buffers lev (lev_half elements each).  A mean may pair the newest
+// level-l sample of the previous launch (the last entry of the level's
+// history) with the first new one.  Every thread reads only rows it wrote
+// itself (its chain and series row); the block synchronises only for the
+// slice folds.
 template <typename T, bool TT>
-__global__ void __launch_bounds__(kCorrThreads)
+__global__ void __launch_bounds__(kCorrThreads, (sizeof(T) == 4 && !TT) ? 2 : 1)
     corr_kernel(const T* __restrict__ ser, int ns, long long n0, int M, int L, T* __restrict__ hist,
                 T* __restrict__ lev, size_t lev_half, double* __restrict__ acc64, double* __restrict__ acc64tt) {
     __shared__ T red[kSliceChains * 96];
@@ -1165,65 +1170,10 @@ __global__ void __launch_bounds__(kCorrThreads)
     const size_t stride = (size_t)M * 6;
     auto cl_of = [&](int l) { return (int)(((n0 + ns) >> l) - (n0 >> l)); };
 
-    // ---- level 0: the raw samples
-    {
-        T* h = hist + (((size_t)mm * L) * 6 + q) * 16;
-        T r[16], acc[16], acc2[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            r[i] = live ? h[i] : T(0);
-            acc[i] = T(0);
-            acc2[i] = T(0);
-        }
-        int nr = 0;
-        const T* yrow = ser + (size_t)mm * 6 + q;
-        corr_ring_products<T, 0, TT>(r, acc, acc2, [&](int j) { return yrow[(size_t)j * stride]; }, ns, src_lane,
-                                     nr);
-        corr_fold_slice(acc, 0, live, fslot, q, acc64 + ((size_t)blockIdx.x * L) * 96, red);
-        if constexpr (TT) corr_fold_slice_tt(acc2, 0, live, fslot, q, acc64tt + ((size_t)blockIdx.x * L) * 48, red);
-        if (live && (L == 1 || cl_of(1) == 0)) {  // no level above brings it up to date
-            T nh[16];
-            corr_ring_newest(r, nr, nh);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) h[i] = nh[i];
-        }
-    }
-
-    // ---- levels 1..: the cprev samples of level l-1 of this launch, yin
-    // (absolute indices pb ..), give the cl samples of level l (absolute nb ..)
-    const T* yin = ser;
-    int cprev = ns;
-    for (int l = 1; l < L; ++l) {
-        const int cl = cl_of(l);
-        if (cl == 0) break;  // no new sample here or above
-        const long long pb = n0 >> (l - 1), nb = n0 >> l;
-        T* yout = lev + (size_t)((l - 1) & 1) * lev_half;
-        const bool last = (l == L - 1) || cl_of(l + 1) == 0;
-        // level l-1: its newest sample before this launch, then its history brought up to date
-        T* hp = hist + (((size_t)mm * L + (l - 1)) * 6 + q) * 16;
-        T old[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) old[i] = live ? hp[i] : T(0);
-        const T* yrow = yin + (size_t)mm * 6 + q;
-        if (live) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int src = cprev - 16 + i;  // position among the new samples
-                hp[i] = src >= 0 ? yrow[(size_t)src * stride] : old[cprev + i];
-            }
-        }
-        // level-l samples: pairs (2J, 2J+1) of level l-1, the first possibly
-        // straddling the launch boundary; stored for level l+1 as they are made
-        const int off = (int)(2 * nb - pb);  // -1 or 0
-        const T pend = old[15];
-        T* orow = yout + (size_t)mm * 6 + q;
-        auto mean = [&](int j) {
-            const int a0 = off + 2 * j;
-            const T v0 = a0 >= 0 ? yrow[(size_t)a0 * stride] : pend;
-            const T v = T(0.5) * (v0 + yrow[(size_t)(a0 + 1) * stride]);
-            if (live) orow[(size_t)j * stride] = v;
-            return v;
-        };
+    const T* yin = ser;  // level-l samples of this launch
+    int cl = ns;
+    for (int l = 0; l < L && cl > 0; ++l) {
+        const int k0 = l == 0 ? 0 : kP / 2;
         T* h = hist + (((size_t)mm * L + l) * 6 + q) * 16;
         T r[16], acc[16], acc2[16];
 #pragma unroll
@@ -1232,19 +1182,36 @@ __global__ void __launch_bounds__(kCorrThreads)
             acc[i] = T(0);
             acc2[i] = T(0);
         }
+        // level-(l+1) sample J is the mean of level-l samples off + 2J and
+        // off + 2J + 1 of this launch; sample -1 is the newest before it
+        const int cn = l + 1 < L ? cl_of(l + 1) : 0;
+        const int off = (int)(2 * (n0 >> (l + 1)) - (n0 >> l));  // -1 or 0
+        T* const yout = lev + (size_t)(l & 1) * lev_half;
+        T* const orow = yout + (size_t)mm * 6 + q;
+        T prev = r[15];
+        auto emit = [&](int a, T y) {
+            const int J = (a - off - 1) >> 1;
+            if (((a - off - 1) & 1) == 0 && J < cn && live) orow[(size_t)J * stride] = T(0.5) * (prev + y);
+            prev = y;
+        };
+        const T* yrow = yin + (size_t)mm * 6 + q;
         int nr = 0;
-        corr_ring_products<T, kP / 2, TT>(r, acc, acc2, mean, cl, src_lane, nr);
-        corr_fold_slice(acc, kP / 2, live, fslot, q, acc64 + ((size_t)blockIdx.x * L + l) * 96, red);
-        if constexpr (TT)
-            corr_fold_slice_tt(acc2, kP / 2, live, fslot, q, acc64tt + ((size_t)blockIdx.x * L + l) * 48, red);
-        if (live && last) {
+        if (l == 0)
+            corr_ring_products<T, 0, TT>(r, acc, acc2, [&](int j) { return yrow[(size_t)j * stride]; }, emit, cl,
+                                         src_lane, nr);
+        else
+            corr_ring_products<T, kP / 2, TT>(r, acc, acc2, [&](int j) { return yrow[(size_t)j * stride]; }, emit,
+                                              cl, src_lane, nr);
+        corr_fold_slice(acc, k0, live, fslot, q, acc64 + ((size_t)blockIdx.x * L + l) * 96, red);
+        if constexpr (TT) corr_fold_slice_tt(acc2, k0, live, fslot, q, acc64tt + ((size_t)blockIdx.x * L + l) * 48, red);
+        if (live) {
             T nh[16];
             corr_ring_newest(r, nr, nh);
 #pragma unroll
             for (int i = 0; i < 16; ++i) h[i] = nh[i];
         }
         yin = yout;
-        cprev = cl;
+        cl = cn;
     }
 }
 
