@@ -63,7 +63,7 @@ extern "C" {
 
 #define SS_CORR_POINTS 16 /* multiple-tau points per level */
 #define SS_MAX_LEVELS 32
-#define SS_MAX_BEADS 128  /* chain length limit of this build             */
+#define SS_MAX_BEADS 128  /* chain length limit of the library           */
 #define SS_MAX_SLOTS 64   /* slip-springs per chain: z_max <= min(N, 64)  */
 
 typedef struct ss_ctx ss_ctx;
