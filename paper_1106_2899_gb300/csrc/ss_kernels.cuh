@@ -161,10 +161,41 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T& n_cos, T
     n_sin = r * s;
 }
 
+// 24-bit uniform in [0, 1) from the low bytes of words x, y, z
+__device__ __forceinline__ uint32_t lo24_bits(uint4 w) {
+    return (w.x & 0xFFu) | ((w.y & 0xFFu) << 8) | ((w.z & 0xFFu) << 16);
+}
 template <typename T>
 __device__ __forceinline__ T uniform_lo24(uint4 w) {
-    const uint32_t lo = (w.x & 0xFFu) | ((w.y & 0xFFu) << 8) | ((w.z & 0xFFu) << 16);
-    return T(lo) * T(1.0 / 16777216.0);
+    return T(lo24_bits(w)) * T(1.0 / 16777216.0);
+}
+
+// ---- packed FP32x2 arithmetic (sm_100 and later: one instruction per pair).
+// Where a lane carries an even number of FP32 beads, the identical scalar
+// operations of two beads (sub-slots 2p and 2p+1) are issued as one packed
+// instruction; each half is rounded exactly as the scalar operation, so the
+// results are bit-identical to the scalar forms.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
+
+// Box-Muller pairs of two beads (words a_k, b_k of bead k), the operations of
+// box_muller<float> on each.
+__device__ __forceinline__ void box_muller_x2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, float& c0,
+                                              float& s0, float& c1, float& s1) {
+    const float2 v = __fmul2_rn(pk(float((a0 >> 8) + 1u), float((a1 >> 8) + 1u)), pk(1.0f / 16777216.0f));
+    const float2 m = __fmul2_rn(pk(__log2f(v.x), __log2f(v.y)), pk(-1.3862943611198906f));
+    const float2 r = __fmul2_rn(m, pk(rsqrtf(fmaxf(m.x, 1e-30f)), rsqrtf(fmaxf(m.y, 1e-30f))));
+    const float2 th = __fmul2_rn(pk(float(int(b0 >> 8) - (1 << 23)), float(int(b1 >> 8) - (1 << 23))),
+                                 pk(3.14159265358979323846f / 8388608.0f));
+    float sa, ca, sb, cb;
+    __sincosf(th.x, &sa, &ca);
+    __sincosf(th.y, &sb, &cb);
+    const float2 cc = __fmul2_rn(r, pk(ca, cb));
+    const float2 ss = __fmul2_rn(r, pk(sa, sb));
+    c0 = cc.x;
+    c1 = cc.y;
+    s0 = ss.x;
+    s1 = ss.y;
 }
 
 template <typename T>
@@ -392,6 +423,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     constexpr int SEGS = 32 / W;
     constexpr int NP = W * B;
     constexpr int G8 = W / 8;        // lanes per value group after seg_reduce8
+    constexpr bool PK = std::is_same<T, float>::value && (B % 2) == 0;  // packed FP32x2 bead pairs
     // per-bead slot masks: 32 bits cover every slot when NP <= 32
     using Mask = typename std::conditional<(NP <= 32), unsigned, unsigned long long>::type;
     const int lane = threadIdx.x & 31;
@@ -534,12 +566,25 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         // ---- random numbers of this step: block (i, t, STEP, chain) per bead/slot i
         T nrm[B][4], u[B];
         const unsigned long long p_shared = philox_step_shared(t, kPurposeStep, c.rk0);
+        if constexpr (PK) {
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const uint4 w = philox_step(ppre[b], p_shared, c.rk0, c.rk1);
-            box_muller<T>(w.x, w.y, nrm[b][0], nrm[b][1]);
-            box_muller<T>(w.z, w.w, nrm[b][2], nrm[b][3]);
-            u[b] = uniform_lo24<T>(w);
+            for (int b = 0; b < B; b += 2) {
+                const uint4 w0 = philox_step(ppre[b], p_shared, c.rk0, c.rk1);
+                const uint4 w1 = philox_step(ppre[b + 1], p_shared, c.rk0, c.rk1);
+                box_muller_x2(w0.x, w0.y, w1.x, w1.y, nrm[b][0], nrm[b][1], nrm[b + 1][0], nrm[b + 1][1]);
+                box_muller_x2(w0.z, w0.w, w1.z, w1.w, nrm[b][2], nrm[b][3], nrm[b + 1][2], nrm[b + 1][3]);
+                const float2 uu = __fmul2_rn(pk(float(lo24_bits(w0)), float(lo24_bits(w1))), pk(1.0f / 16777216.0f));
+                u[b] = uu.x;
+                u[b + 1] = uu.y;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const uint4 w = philox_step(ppre[b], p_shared, c.rk0, c.rk1);
+                box_muller<T>(w.x, w.y, nrm[b][0], nrm[b][1]);
+                box_muller<T>(w.z, w.w, nrm[b][2], nrm[b][3]);
+                u[b] = uniform_lo24<T>(w);
+            }
         }
         __syncwarp();
 #pragma unroll
@@ -606,6 +651,17 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 for (int d = 0; d < 3; ++d) {
                     const T flow = kap[3 * d] * R[b][0] + kap[3 * d + 1] * R[b][1] + kap[3 * d + 2] * R[b][2];
                     Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d]) : T(0);
+                }
+            } else if constexpr (PK) {
+                if ((b & 1) == 0) {  // beads b and b + 1 together
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float2 e = __ffma2_rn(pk(c.amp), pk(nrm[b][d], nrm[b + 1][d]),
+                                                    __ffma2_rn(pk(c.mob), pk(F[b][d], F[b + 1][d]),
+                                                               pk(R[b][d], R[b + 1][d])));
+                        Rn[b][d] = (i < N) ? e.x : T(0);
+                        Rn[b + 1][d] = (i + W < N) ? e.y : T(0);
+                    }
                 }
             } else {
 #pragma unroll

@@ -52,16 +52,19 @@ def _ctx(els, precision, log_every, max_logs, batched):
     return g
 
 
+@pytest.mark.parametrize("flow", [True, False])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_batched_equals_per_element_path(precision):
-    # every lane layout of the batched launch: 16x1, 16x2, 16x3, 16x4, 32x4
+def test_batched_equals_per_element_path(precision, flow):
+    # every lane layout of the batched launch: 16x1, 16x2, 16x3, 16x4, 32x4; with
+    # and without a flow (the step takes different branches)
     els = [(100, 16), (77, 24), (130, 32), (65, 48), (9, 20), (200, 32), (40, 64), (33, 80)]
     elem, frm, kap = _flow_table([m for m, _ in els], 3, 150, seed=1)
     steps, log_every = 500, 50
     out = {}
     for batched in (False, True):
         g = _ctx(els, precision, log_every, steps // log_every, batched)
-        g.set_flow_table(elem, frm, kap)
+        if flow:
+            g.set_flow_table(elem, frm, kap)
         g.run(steps)
         out[batched] = ([g.get_state(e) for e in range(len(els))], [g.log_sums(e) for e in range(len(els))],
                         g.counters())
