@@ -1083,10 +1083,8 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
 // Samples of a level are [j][M][6] arrays (the chain kernel's series for
 // level 0).  hist [M][L][6][16] keeps the newest 16 samples of every level
 // and row (oldest first, zero after a reset): the lags reach back into
-// earlier launches through a 16-entry register ring.  Level l also brings
-// level l-1's history up to date (it needs the old newest sample of level l-1
-// for a pair that straddles the launch boundary); the last level with new
-// samples updates its own.  A CTA covers one slice of
+// earlier launches through a 16-entry register ring; each level's pass
+// writes its own history when it ends.  A CTA covers one slice of
 // kSliceChains chains and adds its chains' sums of this launch, in chain
 // order, to the slice's FP64 sums acc64 [slices][L][3][32] (component,
 // channel * 16 + lag).  With TT the rows of sigma + sigma^(v) also take their
