@@ -389,6 +389,20 @@ __device__ __forceinline__ float hop_prob_fast<float>(const StepConst<float>& c,
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
     return fminf(c.two_pref * r, 0.5f);
 }
+// The same for two moves from one slot (new squared lengths dnew.x, dnew.y),
+// with the additions and multiplications packed; each half is rounded as in
+// hop_prob_fast<float>.
+__device__ __forceinline__ float2 hop_prob_x2(const StepConst<float>& c, float2 dnew, float d_old) {
+    const float2 t = __fmul2_rn(pk(c.c2), __fadd2_rn(dnew, pk(-d_old)));
+    float ea, eb, ra, rb;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ea) : "f"(fminf(t.x, 115.41560327111707f)));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(eb) : "f"(fminf(t.y, 115.41560327111707f)));
+    const float2 den = __fadd2_rn(pk(1.0f), pk(ea, eb));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ra) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rb) : "f"(den.y));
+    const float2 w = __fmul2_rn(pk(c.two_pref), pk(ra, rb));
+    return make_float2(fminf(w.x, 0.5f), fminf(w.y, 0.5f));
+}
 
 // ---------------------------------------------------------- chunk kernel ----
 // W lanes per chain, B beads per lane: bead i and slot i of a chain live on
@@ -705,10 +719,21 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             const T rp[3] = {qp.x - A[b][0], qp.y - A[b][1], qp.z - A[b][2]};
             const T rm[3] = {qm.x - A[b][0], qm.y - A[b][1], qm.z - A[b][2]};
             const T d0 = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2];
-            const T dp = rp[0] * rp[0] + rp[1] * rp[1] + rp[2] * rp[2];
-            const T dm = rm[0] * rm[0] + rm[1] * rm[1] + rm[2] * rm[2];
-            const T pp = (si < N - 1) ? hop_prob_fast<T>(c, dp, d0) : T(0);
-            const T pm = (si > 0) ? hop_prob_fast<T>(c, dm, d0) : T(0);
+            T pp, pm;
+            if constexpr (std::is_same<T, float>::value) {
+                // the moves up and down as one packed pair
+                const float2 dpm = __ffma2_rn(pk(rp[2], rm[2]), pk(rp[2], rm[2]),
+                                              __ffma2_rn(pk(rp[1], rm[1]), pk(rp[1], rm[1]),
+                                                         __fmul2_rn(pk(rp[0], rm[0]), pk(rp[0], rm[0]))));
+                const float2 ppm = hop_prob_x2(c, dpm, d0);
+                pp = (si < N - 1) ? ppm.x : T(0);
+                pm = (si > 0) ? ppm.y : T(0);
+            } else {
+                const T dp = rp[0] * rp[0] + rp[1] * rp[1] + rp[2] * rp[2];
+                const T dm = rm[0] * rm[0] + rm[1] * rm[1] + rm[2] * rm[2];
+                pp = (si < N - 1) ? hop_prob_fast<T>(c, dp, d0) : T(0);
+                pm = (si > 0) ? hop_prob_fast<T>(c, dm, d0) : T(0);
+            }
             bool up = occ && (u[b] < pp);
             bool dn = occ && !up && (u[b] < pp + pm);
             if (tmode == 2) {
