@@ -591,6 +591,13 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 u[b] = uu.x;
                 u[b + 1] = uu.y;
             }
+        } else if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {  // the bead's two Box-Muller pairs packed
+                const uint4 w = philox_step(ppre[b], p_shared, c.rk0, c.rk1);
+                box_muller_x2(w.x, w.y, w.z, w.w, nrm[b][0], nrm[b][1], nrm[b][2], nrm[b][3]);
+                u[b] = uniform_lo24<T>(w);
+            }
         } else {
 #pragma unroll
             for (int b = 0; b < B; ++b) {
@@ -917,15 +924,34 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 const Pos<T> p1 = pos[i < N - 1 ? i + 1 : i];
                 // the last bead reads itself (q = 0)
                 const T q[3] = {p1.x - R[b][0], p1.y - R[b][1], p1.z - R[b][2]};
-                const T kq0 = c.k_b * q[0], kq1 = c.k_b * q[1];
-                v[0] += kq0 * q[1];
-                v[1] += kq0 * q[2];
-                v[2] += kq1 * q[2];
-                if (b * W < zn) {  // springs (an empty slot's d is 0)
-                    const T kd0 = c.k_s * dd[b][0], kd1 = c.k_s * dd[b][1];
-                    v[3] += kd0 * dd[b][1];
-                    v[4] += kd0 * dd[b][2];
-                    v[5] += kd1 * dd[b][2];
+                T kq0, kq1;
+                if constexpr (std::is_same<T, float>::value) {  // (xy, xz) as a packed pair
+                    const float2 kq = __fmul2_rn(pk(c.k_b), pk(q[0], q[1]));
+                    kq0 = kq.x;
+                    kq1 = kq.y;
+                    const float2 v01 = __ffma2_rn(pk(kq0), pk(q[1], q[2]), pk(v[0], v[1]));
+                    v[0] = v01.x;
+                    v[1] = v01.y;
+                    v[2] += kq1 * q[2];
+                    if (b * W < zn) {  // springs (an empty slot's d is 0)
+                        const float2 kd = __fmul2_rn(pk(c.k_s), pk(dd[b][0], dd[b][1]));
+                        const float2 v34 = __ffma2_rn(pk(kd.x), pk(dd[b][1], dd[b][2]), pk(v[3], v[4]));
+                        v[3] = v34.x;
+                        v[4] = v34.y;
+                        v[5] += kd.y * dd[b][2];
+                    }
+                } else {
+                    kq0 = c.k_b * q[0];
+                    kq1 = c.k_b * q[1];
+                    v[0] += kq0 * q[1];
+                    v[1] += kq0 * q[2];
+                    v[2] += kq1 * q[2];
+                    if (b * W < zn) {  // springs (an empty slot's d is 0)
+                        const T kd0 = c.k_s * dd[b][0], kd1 = c.k_s * dd[b][1];
+                        v[3] += kd0 * dd[b][1];
+                        v[4] += kd0 * dd[b][2];
+                        v[5] += kd1 * dd[b][2];
+                    }
                 }
                 if (do_log) {
                     dgp[0] += kq0 * q[0];
