@@ -52,7 +52,7 @@ SMS, LANES_PER_SM, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
 # DRAM bytes (read + write) of one chain-kernel launch of 1024 steps, per chain:
 # ncu capture of 16384 chains x 1024 steps (profiles/chunk_kernel_16x2_small_full.md),
 # 17.3 MB read + 363.5 MB written; every term scales with the chain count.
-TRAFFIC_BYTES_PER_CHAIN_1024 = 378.5e6 / 16384
+TRAFFIC_BYTES_PER_CHAIN_1024 = 380.5e6 / 16384
 
 
 def _peaks():
