@@ -52,7 +52,7 @@ SMS, LANES_PER_SM, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
 # DRAM bytes (read + write) of one chain-kernel launch of 1024 steps, per chain:
 # ncu capture of 16384 chains x 1024 steps (profiles/chunk_kernel_16x2_small_full.md),
 # 17.3 MB read + 363.5 MB written; every term scales with the chain count.
-TRAFFIC_BYTES_PER_CHAIN_1024 = 380.5e6 / 16384
+TRAFFIC_BYTES_PER_CHAIN_1024 = 380.2e6 / 16384
 
 
 def _peaks():
@@ -272,7 +272,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-ops/s",
                      "frac": achieved / peak,
                      "traffic": TRAFFIC_BYTES_PER_CHAIN_1024 * M if abs(steps_per_launch - 1024) < 1e-9 else None,
-                     "kernel": "chunk_kernel<float, 16, 2, 0>", "kernel_ms": kernel_ms,
+                     "kernel": "chunk_kernel<float, 16, 2, 0, 0>", "kernel_ms": kernel_ms,
                      "kernel_share_of_region": chain_ms / ms_total if ws == 1 else None,
                      "alg_ops_per_bead_step": ALG_OPS_PER_BEAD_STEP,
                      "peak_basis": "152 SMs x 128 lanes x 2070 MHz (nominal max clock), 1 lane-op/lane/clock"},

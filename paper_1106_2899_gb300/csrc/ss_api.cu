@@ -270,6 +270,21 @@ int corr_launches(const T* ser, int ns, int M, int L, long long n0, T* hist, dou
                    : corr_launches_t<T, false>(ser, ns, M, L, n0, hist, acc64, nullptr, lev, lev_half, st);
 }
 
+// Whether element e has a nonzero velocity gradient at any step of t0 ..
+// t0 + nsteps - 1 (the schedule entry active at t0 and every entry that starts
+// inside the window, as the chain kernel walks them).
+bool flow_in_window(const Elem& e, long long t0, int nsteps) {
+    const int n = (int)e.kfrom.size();
+    int ki = 0;
+    while (ki + 1 < n && t0 >= e.kfrom[ki + 1]) ++ki;
+    for (int k = ki; k < n; ++k) {
+        if (k > ki && e.kfrom[k] >= t0 + nsteps) break;
+        for (int d = 0; d < 9; ++d)
+            if (e.kap[9 * (size_t)k + d] != 0.0) return true;
+    }
+    return false;
+}
+
 template <typename T, int W, int B>
 int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     NvtxRange range("chain kernel + correlator launch");
@@ -334,14 +349,22 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         a.snap_steps = c->win.ce;
     }
     const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, a.nlog_chunk);
-    // differentiation windows run the instantiation with the window hooks
+    // differentiation windows run the instantiation with the window hooks; an
+    // FP32 launch without a velocity gradient the one without the flow terms
     const bool win = c->opt_tape_mode != 0 || c->opt_snap;
     void (*kern)(const ssk::ChunkArgs, const ssk::StepConst<T>) =
-        win ? ssk::chunk_kernel<T, W, B, true> : ssk::chunk_kernel<T, W, B, false>;
-    static int configured_bytes[2] = {0, 0};
-    if (plan.total > 48 * 1024 && plan.total > configured_bytes[win]) {
+        win ? ssk::chunk_kernel<T, W, B, true, true> : ssk::chunk_kernel<T, W, B, false, true>;
+    int variant = win ? 1 : 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (!win && !flow_in_window(e, t0, nsteps)) {
+            kern = ssk::chunk_kernel<T, W, B, false, false>;
+            variant = 2;
+        }
+    }
+    static int configured_bytes[3] = {0, 0, 0};
+    if (plan.total > 48 * 1024 && plan.total > configured_bytes[variant]) {
         SS_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
-        configured_bytes[win] = plan.total;
+        configured_bytes[variant] = plan.total;
     }
     const ssk::StepConst<T> sc = step_const<T>(c, e.N);
     const int ctas = (e.M + chains_per_cta(W) - 1) / chains_per_cta(W);
@@ -1726,7 +1749,7 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
     }
     const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, 0);
     if (plan.total > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(ssk::chunk_kernel<T, W, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(ssk::chunk_kernel<T, W, B, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              plan.total);
         if (e != cudaSuccess) return SS_ECUDA;
     }
@@ -1736,7 +1759,7 @@ int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint
         const int ns = (int)std::min<int64_t>(n_steps - done, c->levels > 0 ? ser_cap : p.chunk_steps);
         a.t0 = t0 + done;
         a.nsteps = ns;
-        ssk::chunk_kernel<T, W, B, false><<<(M + chains_per_cta(W) - 1) / chains_per_cta(W), kThreads, plan.total, st>>>(a, sc);
+        ssk::chunk_kernel<T, W, B, false, true><<<(M + chains_per_cta(W) - 1) / chains_per_cta(W), kThreads, plan.total, st>>>(a, sc);
         if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
         if (c->levels > 0 &&
             corr_launches<T>(static_cast<const T*>(a.series), ns, M, c->levels, done,

@@ -430,7 +430,9 @@ __device__ __forceinline__ void snapshot_store(const ChunkArgs& a, long long row
 
 // The chains of one CTA: chains cta_first .. cta_first + chains per CTA - 1 of
 // the element described by `a` (all warps of the CTA call this together).
-template <typename T, int W, int B, bool WIN>
+// FLOW: the velocity-gradient terms are compiled in (without them the launch
+// must have kappa = 0 throughout; recentring is then never needed).
+template <typename T, int W, int B, bool WIN, bool FLOW>
 __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T>& c, const int cta_first,
                                            const T NkT, const long long t0_, const int nsteps_,
                                            const long long log_m0_, const int nlog_) {
@@ -507,15 +509,18 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         return r > (long long)never ? never : (int)r;
     };
     int ki = 0;
-    while (ki + 1 < a.n_kap && t0_ >= a.kap_from[ki + 1]) ++ki;
     T kap[9];
     bool kap_nz = false;
+    int next_from = never;
+    if constexpr (FLOW) {
+        while (ki + 1 < a.n_kap && t0_ >= a.kap_from[ki + 1]) ++ki;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        kap[i] = T(a.kap[ki * 9 + i]);
-        kap_nz |= (kap[i] != T(0));
+        for (int i = 0; i < 9; ++i) {
+            kap[i] = T(a.kap[ki * 9 + i]);
+            kap_nz |= (kap[i] != T(0));
+        }
+        next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
     }
-    int next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
     int next_log = a.log_every > 0 ? rel((t0_ / a.log_every + 1) * a.log_every - 1) : never;
     int next_rc = a.recenter_every > 0 ? rel((t0_ / a.recenter_every + 1) * a.recenter_every - 1) : never;
     int log_slot = 0;
@@ -554,7 +559,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 
     for (int s = 0; s < nsteps_; ++s) {
         const uint32_t t = t0lo + (uint32_t)s;
-        if (s >= next_from) {
+        if (FLOW && s >= next_from) {
             while (ki + 1 < a.n_kap && t0_ + s >= a.kap_from[ki + 1]) ++ki;
             kap_nz = false;
 #pragma unroll
@@ -668,10 +673,39 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
             if (kap_nz) {
+                if constexpr (PK) {
+                    // beads b and b + 1 together; the same operations as the FP32 form below
+                    if ((b & 1) == 0) {
+                        const float2 r0 = pk(R[b][0], R[b + 1][0]), r1 = pk(R[b][1], R[b + 1][1]),
+                                     r2 = pk(R[b][2], R[b + 1][2]);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const T flow = kap[3 * d] * R[b][0] + kap[3 * d + 1] * R[b][1] + kap[3 * d + 2] * R[b][2];
-                    Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d]) : T(0);
+                        for (int d = 0; d < 3; ++d) {
+                            const float2 flow = __ffma2_rn(pk(kap[3 * d + 2]), r2,
+                                                           __ffma2_rn(pk(kap[3 * d + 1]), r1,
+                                                                      __fmul2_rn(pk(kap[3 * d]), r0)));
+                            const float2 e = __ffma2_rn(
+                                pk(c.amp), pk(nrm[b][d], nrm[b + 1][d]),
+                                __ffma2_rn(pk(c.dt), flow,
+                                           __ffma2_rn(pk(c.mob), pk(F[b][d], F[b + 1][d]), pk(R[b][d], R[b + 1][d]))));
+                            Rn[b][d] = (i < N) ? e.x : T(0);
+                            Rn[b + 1][d] = (i + W < N) ? e.y : T(0);
+                        }
+                    }
+                } else if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float flow = __fmaf_rn(kap[3 * d + 2], R[b][2],
+                                                     __fmaf_rn(kap[3 * d + 1], R[b][1], __fmul_rn(kap[3 * d], R[b][0])));
+                        Rn[b][d] = (i < N) ? __fmaf_rn(c.amp, nrm[b][d],
+                                                       __fmaf_rn(c.dt, flow, __fmaf_rn(c.mob, F[b][d], R[b][d])))
+                                           : T(0);
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const T flow = kap[3 * d] * R[b][0] + kap[3 * d + 1] * R[b][1] + kap[3 * d + 2] * R[b][2];
+                        Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d]) : T(0);
+                    }
                 }
             } else if constexpr (PK) {
                 if ((b & 1) == 0) {  // beads b and b + 1 together
@@ -1081,11 +1115,14 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 }
 
 // WIN: the differentiation-window hooks (decision tape, snapshots, stress
-// series) are compiled in; the plain kernel carries none of them.
-template <typename T, int W, int B, bool WIN>
+// series) are compiled in; the plain kernel carries none of them.  FLOW: the
+// velocity-gradient terms are compiled in (launches with kappa = 0 throughout
+// may use the instantiation without them).
+template <typename T, int W, int B, bool WIN, bool FLOW>
 __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : (B >= 4 ? 4 : SS_CTAS_PER_SM_MULTI))
     chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
-    run_chains<T, W, B, WIN>(a, c, blockIdx.x * (kChunkThreads / W), c.NkT, a.t0, a.nsteps, a.log_m0, a.nlog_chunk);
+    run_chains<T, W, B, WIN, FLOW>(a, c, blockIdx.x * (kChunkThreads / W), c.NkT, a.t0, a.nsteps, a.log_m0,
+                                   a.nlog_chunk);
 }
 
 // ------------------------------------------------------ batched kernel ------
@@ -1115,7 +1152,7 @@ __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CT
         const int2 wi = items[it];
         const ChunkArgs& a = elems[wi.x];
         const int nlog = a.log_every > 0 ? (int)((info.t0 + info.nsteps) / a.log_every - info.t0 / a.log_every) : 0;
-        run_chains<T, W, B, false>(a, c, wi.y, T((double)a.N) * c.kT, info.t0, info.nsteps, info.log_m0, nlog);
+        run_chains<T, W, B, false, true>(a, c, wi.y, T((double)a.N) * c.kT, info.t0, info.nsteps, info.log_m0, nlog);
     }
 }
 
