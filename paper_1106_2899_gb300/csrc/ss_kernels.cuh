@@ -1045,6 +1045,23 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 pn.w = T(0);
                 pos[i] = pn;
             }
+            // the spring vectors from the shifted coordinates, as a launch
+            // starting here computes them: results do not depend on where the
+            // launches end
+            __syncwarp();
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int i = ll + b * W;
+                if (i < Z) {
+                    const Pos<T> ps = pos[S[b]];
+                    SlotRec<T> rec;
+                    rec.x = ps.x - A[b][0];
+                    rec.y = ps.y - A[b][1];
+                    rec.z = ps.z - A[b][2];
+                    rec.s = S[b];
+                    tab[i] = rec;
+                }
+            }
         }
         __syncwarp();
     }

@@ -10,6 +10,10 @@
 * Steady shear at N = 80 (Sec. 4.1): the average number of slip-springs the
   paper prints for gdot = 0.01, 0.1, 1 (8.7, 4.2, 1.6, against 20 at
   equilibrium), within 15% (measured: 8.6, 4.2, 1.7).
+* A flow that starts inside a launch: FP32 launches whose velocity gradient is
+  zero at every step run an instantiation without the flow terms, so the same
+  schedule stepped in launches of different lengths (the start of the flow
+  inside a launch, or on a launch boundary) must give bit-identical states.
 * Linear response (Sec. 2.3, Eqs. single_chain_time_depending_stress_expression_final
   and relaxation_modulus_tensor_green_kubo_form): for a step of simple shear
   of small rate, eta+(t) = integral_0^t G_TOTAL(s) ds, with G_TOTAL = AUTO +
@@ -180,3 +184,25 @@ def test_steady_shear_number_of_slip_springs_at_N80():
         assert abs(got[gd] - printed[gd]) <= 0.15 * printed[gd], (gd, got[gd], printed[gd])
     print("\nsteady shear, N=80: <Z> = %s (paper: %s)" % (
         {k: round(v, 2) for k, v in got.items()}, printed))
+
+
+@pytest.mark.parametrize("N", [32, 16])
+def test_flow_start_inside_a_launch_is_bit_identical(N):
+    kap = np.zeros((3, 3))
+    kap[0, 1] = 0.05
+    kap2 = np.diag([0.02, -0.01, -0.01])
+    states = []
+    for chunk in (1000, 500, 250):
+        g = SlipSpring([(300, N)], precision="fp32", seed=9)
+        g.set_params(**synth.PAPER, corr_levels=8, groups=4, chunk_steps=chunk, recenter_every=100)
+        g.set_flow(kap, 1500)   # inside a 1000-step launch, on a 500-step boundary
+        g.set_flow(kap2, 2750)  # inside the 1000- and 500-step launches
+        g.run(3200)
+        assert g.status() == 0
+        states.append((g.get_state(), g.counters()))
+    (a, ca) = states[0]
+    for b, cb in states[1:]:
+        for k in ("Z", "S", "R", "A"):
+            assert np.array_equal(a[k], b[k]), k
+        for k in ("hops_up", "hops_down", "created", "destroyed"):
+            assert ca[k] == cb[k], k
