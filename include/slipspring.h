@@ -105,7 +105,11 @@ typedef struct {
                                one-step-per-launch form.  With the correlator on, a
                                launch covers at most 1024 steps (larger values are
                                reduced to 1024): the launch's stress series, 24 B per
-                               chain and step in FP32, is what the correlator reads */
+                               chain and step in FP32, is what the correlator reads.
+                               The chain states and event counts do not depend on it
+                               (random numbers are indexed by the absolute step); the
+                               correlator folds its FP32 sums of each launch into FP64,
+                               so its sums depend on it at the rounding level        */
     int32_t corr_tt;        /* 1: also correlate sigma + sigma^(v) with itself (channels
                                SS_CH_TT, SS_CH_VIRTUAL) [0]                             */
 } ss_params;
