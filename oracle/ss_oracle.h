@@ -96,7 +96,11 @@ typedef struct {
  * (dR_a/dt contains kappa[a][b] R_b).  cd = Phi^{-1}(p_destroy) (the destroy
  * decision threshold on the block's fourth normal; +inf if p_destroy = 1).
  * Pinned by the Rouse closed form, the equilibrium invariants, hop detailed
- * balance and brute-force enumeration. */
+ * balance and brute-force enumeration; its flow terms (kappa . R in the bead
+ * update, affine anchor advection) by the frozen-bead linear map
+ * (I + dt kappa)^n and the sheared-Rouse Lyapunov solution; the anchor spread
+ * of new springs by the spring-vector variance kT/k_s in the dynamics.  Each of
+ * these pins is shown to fail on a copy with a planted mistake. */
 void or_step_chain(const or_params* p, const uint32_t key[2], uint32_t chain_id, uint32_t step,
                    const double kappa[9], double cd, or_chain* c, or_step_info* info);
 
@@ -136,7 +140,9 @@ or_ens* or_ens_create(const or_params* p, uint64_t seed, int M, uint32_t chain_o
                       int levels, int log_every, int max_logs);
 void or_ens_destroy(or_ens* e);
 void or_ens_init(or_ens* e);
-/* piecewise-constant kappa from step `from_step` on (replaces later entries) */
+/* piecewise-constant kappa from step `from_step` on (replaces later entries):
+ * the step t -> t+1 uses the entry with the largest from_step <= t.  Pinned
+ * by the schedule-switch closed form. */
 int or_ens_set_flow(or_ens* e, int64_t from_step, const double kappa[9]);
 /* Run n_steps.  Optional per-step traces (NULL to skip): Z_tr[n_steps][M],
  * S_tr[n_steps][M][z_max] (-1 for empty slots), margin_tr[n_steps][M]. */
