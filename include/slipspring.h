@@ -56,7 +56,7 @@ extern "C" {
 #define SS_CH_AUTO 0  /* (1/N) <sigma_ab(t) sigma_ab(0)>                 */
 #define SS_CH_CROSS 1 /* (1/N) <sigma_ab(t) sigma^(v)_ab(0)>             */
 #define SS_CH_TOTAL 2 /* AUTO + CROSS: the paper's G(t)                   */
-/* with corr_tt = 1 (Sec. 4.2, Eq. relative_contribution_virtual_stress_to_
+/* with corr_tt = 1 (Sec. 4.1, Eq. relative_contribution_virtual_stress_to_
  * shear_relaxation_modulus: the virtual-stress share is VIRTUAL / TOTAL) */
 #define SS_CH_TT 3      /* (1/N) <(sigma + sigma^(v))_ab(t) (sigma + sigma^(v))_ab(0)> */
 #define SS_CH_VIRTUAL 4 /* TT - TOTAL = (1/N) <sigma^(v)_ab(t) (sigma + sigma^(v))_ab(0)> */
@@ -198,6 +198,33 @@ int ss_get_state(ss_ctx* ctx, int elem, double* R, int32_t* Z, int32_t* S, doubl
 int ss_set_state(ss_ctx* ctx, int elem, const double* R, const int32_t* Z, const int32_t* S,
                  const double* A);
 
+/* The same two calls on caller-owned DEVICE arrays in the same layout as
+ * ss_get_state / ss_set_state (R [M][N][3] and A [M][z_max][3] double, S
+ * [M][z_max] and Z [M] int32; the state converted to and from the library's
+ * device layout by kernels, in FP64 whatever the precision), for callers whose
+ * data already lives on the GPU (e.g. torch tensors).  cuda_stream: the
+ * caller's cudaStream_t, or NULL for the context's stream.
+ * ss_get_state_dev is asynchronous: the copy is ordered after the work already
+ * enqueued on the context's stream, and work the caller enqueues on
+ * cuda_stream afterwards sees the arrays written; any array may be NULL.
+ * ss_set_state_dev waits on the context's stream for work already enqueued on
+ * cuda_stream, validates the arrays as ss_set_state does (synchronising the
+ * context's stream to read a 4-byte check flag) and replaces the state; the
+ * caller's arrays may be reused when it returns.  Errors as ss_set_state. */
+int ss_get_state_dev(ss_ctx* ctx, int elem, double* R, int32_t* Z, int32_t* S, double* A, void* cuda_stream);
+int ss_set_state_dev(ss_ctx* ctx, int elem, const double* R, const int32_t* Z, const int32_t* S,
+                     const double* A, void* cuda_stream);
+
+/* Histogram of the slip-spring number Z over the chains of element elem (the
+ * distribution of Eq. slip_spring_number_distribution_modified, Poisson(N/N0)
+ * in equilibrium up to the z_max cap and the O(dt) bias of the scheme):
+ * hist[z] = number of chains with Z = z, z = 0..z_max.  *n_out = z_max + 1;
+ * with hist NULL or cap = 0 only *n_out is set.  Counted on the device, read
+ * back once: synchronises.  SS_ESTATE before the state exists; SS_EOVERFLOW if
+ * some chain's Z lies outside 0..z_max (a broken invariant, see ss_status;
+ * those chains are in no bin). */
+int ss_zhist(ss_ctx* ctx, int elem, int64_t* hist, int cap, int* n_out);
+
 /* Global chain id of chain 0 of element 0 (default 0); the elements follow
  * contiguously.  A shard of a larger ensemble (one GPU or process of several)
  * passes the start of its contiguous chain range, so that every chain draws
@@ -292,9 +319,10 @@ int ss_window_backward(ss_ctx* ctx, const double* dL_dG, double grad[3]);
 
 /* ---- allocation-free run ---------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot
- * call cudaMalloc: code that runs while a CUDA graph is being captured, code
- * inside a host that owns all device memory through its own pool, and
- * real-time loops where an allocation could block.  It advances caller-owned
+ * call cudaMalloc: a host application that owns all device memory through its
+ * own pool and forbids allocations behind its back, a framework whose device
+ * memory budget is fixed when it starts, and real-time loops in which an
+ * allocation could block or synchronise the device.  It advances caller-owned
  * device state by n_steps with the same chain and correlator kernels as
  * ss_run, and keeps their working memory (correlator history and FP64 sums,
  * the stress series of a launch and the correlator's level samples, event
@@ -310,8 +338,10 @@ int ss_window_backward(ss_ctx* ctx, const double* dL_dG, double grad[3]);
  *   SS_FP64; entries beyond n_beads / beyond Z are ignored), S [n_chains][NP]
  *   int32 bead index of slot j (j < Z), Z [n_chains] int32.
  * params: as ss_set_params (log_every must be 0; chunk_steps splits the call
- *   into launches; channel TT is not accumulated); z_max <= min(n_beads, 64).  kappa: row-major constant velocity
- *   gradient for the whole call (host array), NULL for none.
+ *   into launches; channel TT is not accumulated); z_max <= min(n_beads, 64).
+ * kappa: row-major constant velocity gradient for the whole call (host array,
+ *   read during the call and handed to the GPU by value in a kernel's
+ *   arguments), NULL for none.
  * seed, chain_base, t0: Philox key, global id of chain 0 and the index of the
  *   first step, so that consecutive calls with t0 advanced by n_steps draw the
  *   same numbers as one ss_run of the same chains.

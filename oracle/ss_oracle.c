@@ -399,7 +399,7 @@ void or_stress(const or_params* p, const or_chain* c, double sig[9], double sigv
  * Channel 0 accumulates later sigma times origin sigma (AUTO); channel 1 later
  * sigma times origin sigma + sigma_v (TOTAL); the optional channel TT (acc_tt)
  * later sigma + sigma_v times origin sigma + sigma_v, whose difference with
- * TOTAL is the virtual-stress numerator of Sec. 4.2 (Eq.
+ * TOTAL is the virtual-stress numerator of Sec. 4.1 (Eq.
  * relative_contribution_virtual_stress_to_shear_relaxation_modulus). */
 typedef struct {
     double hist[OR_LMAX][OR_P][6];

@@ -22,7 +22,8 @@ EXPORTS = ["ss_create", "ss_set_params", "ss_set_flow", "ss_run", "ss_stress", "
            "ss_reset_observables", "ss_corr_sums", "ss_log_sums", "ss_counters", "ss_status",
            "ss_synchronize", "ss_run_noalloc", "ss_kernel_timing", "ss_kernel_time",
            "ss_set_chain_offset", "ss_set_flow_table", "ss_set_batched", "ss_window_forward",
-           "ss_window_backward", "ss_set_coefficients", "ss_set_step_count", "ss_corr_sums_tt"]
+           "ss_window_backward", "ss_set_coefficients", "ss_set_step_count", "ss_corr_sums_tt",
+           "ss_get_state_dev", "ss_set_state_dev", "ss_zhist"]
 
 
 class ss_element(C.Structure):
@@ -84,6 +85,9 @@ def load(path: str = LIB_PATH):
         "ss_set_step_count": [vp, C.c_int64],
         "ss_corr_sums_tt": [vp, C.c_int, dp, P(C.c_int), i64p],
         "ss_kernel_time": [vp, dp, i64p],
+        "ss_get_state_dev": [vp, C.c_int, vp, vp, vp, vp, vp],
+        "ss_set_state_dev": [vp, C.c_int, vp, vp, vp, vp, vp],
+        "ss_zhist": [vp, C.c_int, i64p, C.c_int, P(C.c_int)],
         "ss_run_noalloc": [P(ss_params), C.c_int, C.c_uint64, C.c_int32, C.c_int32, C.c_uint32, C.c_int64,
                            C.c_int64, dp, vp, vp, vp, vp, vp, vp, vp],
     }

@@ -147,7 +147,28 @@ class SlipSpring:
         self._chk(self.lib.ss_set_state(self.h, elem, _p(R, C.c_double), _p(Z, C.c_int32), _p(S, C.c_int32),
                                         _p(A, C.c_double)), "ss_set_state")
 
+    def get_state_dev(self, R, Z, S, A, elem=0, stream=None):
+        """Copy the state into caller-owned CUDA tensors (R [M][N][3], A [M][z_max][3]
+        float64; S [M][z_max], Z [M] int32), ordered before later work on `stream`."""
+        st = C.c_void_p(int(stream)) if stream is not None else None
+        ptr = [C.c_void_p(t.data_ptr()) if t is not None else None for t in (R, Z, S, A)]
+        self._chk(self.lib.ss_get_state_dev(self.h, elem, *ptr, st), "ss_get_state_dev")
+
+    def set_state_dev(self, R, Z, S, A, elem=0, stream=None):
+        """Replace the state from CUDA tensors laid out as in get_state_dev."""
+        st = C.c_void_p(int(stream)) if stream is not None else None
+        ptr = [C.c_void_p(t.data_ptr()) for t in (R, Z, S, A)]
+        self._chk(self.lib.ss_set_state_dev(self.h, elem, *ptr, st), "ss_set_state_dev")
+
     # ------------------------------------------------------ observables ---
+    def zhist(self, elem=0):
+        """Histogram of the slip-spring number Z over the element's chains, z = 0..z_max."""
+        n = C.c_int()
+        self._chk(self.lib.ss_zhist(self.h, elem, None, 0, C.byref(n)), "ss_zhist")
+        h = np.zeros(n.value, dtype=np.int64)
+        self._chk(self.lib.ss_zhist(self.h, elem, _p(h, C.c_int64), n.value, C.byref(n)), "ss_zhist")
+        return h
+
     def stress(self, elem=0):
         """(t, mean[n][6], sem[n][6]) of sigma xx,yy,zz,xy,xz,yz at the log times."""
         n = C.c_int()

@@ -118,6 +118,7 @@ struct ss_ctx {
     int opt_tape_mode = 0;
     bool opt_snap = false, opt_series = false, opt_corr_off = false;
     long long opt_snap_t0 = 0;
+    cudaEvent_t xev = nullptr;  // orders the context's stream against a caller's stream
     std::string err;
 };
 
@@ -354,18 +355,13 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     const bool win = c->opt_tape_mode != 0 || c->opt_snap;
     void (*kern)(const ssk::ChunkArgs, const ssk::StepConst<T>) =
         win ? ssk::chunk_kernel<T, W, B, true, true> : ssk::chunk_kernel<T, W, B, false, true>;
-    int variant = win ? 1 : 0;
     if constexpr (std::is_same<T, float>::value) {
-        if (!win && !flow_in_window(e, t0, nsteps)) {
-            kern = ssk::chunk_kernel<T, W, B, false, false>;
-            variant = 2;
-        }
+        if (!win && !flow_in_window(e, t0, nsteps)) kern = ssk::chunk_kernel<T, W, B, false, false>;
     }
-    static int configured_bytes[3] = {0, 0, 0};
-    if (plan.total > 48 * 1024 && plan.total > configured_bytes[variant]) {
+    // the attribute belongs to the current device: set it on every launch that
+    // needs more than the default 48 KiB (a host call per launch of many steps)
+    if (plan.total > 48 * 1024)
         SS_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
-        configured_bytes[variant] = plan.total;
-    }
     const ssk::StepConst<T> sc = step_const<T>(c, e.N);
     const int ctas = (e.M + chains_per_cta(W) - 1) / chains_per_cta(W);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -507,6 +503,10 @@ int get_state_t(ss_ctx* c, Elem& e, double* R, int32_t* Z, int32_t* S, double* A
 }
 
 template <typename T>
+int check_convert_state(ss_ctx* c, Elem& e, const double* dR, const double* dA, const int32_t* dS, const int32_t* dZ,
+                        int* dF);
+
+template <typename T>
 int set_state_t(ss_ctx* c, Elem& e, const double* R, const int32_t* Z, const int32_t* S, const double* A) {
     // the caller's arrays go to the device as they are; checked and converted there
     const size_t M = e.M, N = e.N, zm = e.zmax;
@@ -526,6 +526,16 @@ int set_state_t(ss_ctx* c, Elem& e, const double* R, const int32_t* Z, const int
     SS_CUDA(c, cudaMemcpyAsync(st + oA, A, bA, cudaMemcpyHostToDevice, c->stream));
     SS_CUDA(c, cudaMemcpyAsync(st + oS, S, bS, cudaMemcpyHostToDevice, c->stream));
     SS_CUDA(c, cudaMemcpyAsync(st + oZ, Z, bZ, cudaMemcpyHostToDevice, c->stream));
+    return check_convert_state<T>(c, e, dR, dA, dS, dZ, dF);
+}
+
+// Check a state in the caller's layout held in device memory (dR [M][N][3],
+// dA [M][zm][3] double, dS [M][zm], dZ [M] int32) and, if it is valid, convert
+// it into the element's device layout.  dF: a device int used as the check
+// flag.  Synchronises the context's stream to read the flag.
+template <typename T>
+int check_convert_state(ss_ctx* c, Elem& e, const double* dR, const double* dA, const int32_t* dS, const int32_t* dZ,
+                        int* dF) {
     SS_CUDA(c, cudaMemsetAsync(dF, 0, sizeof(int), c->stream));
     const int width = std::max(e.N, e.zmax);
     const long long nchk = (long long)e.M * width, ncv = (long long)e.M * e.NP;
@@ -1096,6 +1106,17 @@ int window_backward_t(ss_ctx* c, const double* dL_dG, double grad[3]) {
 }  // namespace
 
 // ================================================================== C ABI ====
+namespace {
+// Work enqueued on `later` from now on runs after what is enqueued on `first`.
+int order_streams(ss_ctx* c, cudaStream_t first, cudaStream_t later) {
+    if (first == later) return SS_OK;
+    if (!c->xev) SS_CUDA(c, cudaEventCreateWithFlags(&c->xev, cudaEventDisableTiming));
+    SS_CUDA(c, cudaEventRecord(c->xev, first));
+    SS_CUDA(c, cudaStreamWaitEvent(later, c->xev, 0));
+    return SS_OK;
+}
+}  // namespace
+
 extern "C" {
 
 int ss_create(ss_ctx** out, const ss_element* elems, int n_elems, int precision, uint64_t seed,
@@ -1408,6 +1429,7 @@ int ss_destroy(ss_ctx* c) {
     if (c->counters) cudaFree(c->counters);
     if (c->status) cudaFree(c->status);
     if (c->stage) cudaFree(c->stage);
+    if (c->xev) cudaEventDestroy(c->xev);
     delete c;
     return SS_OK;
 }
@@ -1439,6 +1461,78 @@ int ss_set_state(ss_ctx* c, int elem, const double* R, const int32_t* Z, const i
         }
         c->initialized = true;
     }
+    return SS_OK;
+}
+
+// ---- the state through caller-owned device memory, the Z histogram
+int ss_get_state_dev(ss_ctx* c, int elem, double* R, int32_t* Z, int32_t* S, double* A, void* cuda_stream) {
+    Elem* e = elem_at(c, elem);
+    if (!e) return fail(c, SS_EINVAL, "bad element");
+    if (!c->have_params) return fail(c, SS_ESTATE, "no parameters");
+    if (!R && !Z && !S && !A) return SS_OK;
+    const int width = std::max(e->N, e->zmax);
+    const unsigned blocks = (unsigned)(((long long)e->M * width + 255) / 256);
+    if (c->prec == SS_FP64)
+        ssk::state_export_kernel<double><<<blocks, 256, 0, c->stream>>>(
+            static_cast<const double*>(e->R), static_cast<const double*>(e->A), e->S, e->Z, e->M, e->N, e->zmax,
+            e->NP, R, A, S, Z);
+    else
+        ssk::state_export_kernel<float><<<blocks, 256, 0, c->stream>>>(
+            static_cast<const float*>(e->R), static_cast<const float*>(e->A), e->S, e->Z, e->M, e->N, e->zmax,
+            e->NP, R, A, S, Z);
+    SS_CUDA(c, cudaGetLastError());
+    c->launches++;
+    const cudaStream_t user = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+    return order_streams(c, c->stream, user);
+}
+
+int ss_set_state_dev(ss_ctx* c, int elem, const double* R, const int32_t* Z, const int32_t* S, const double* A,
+                     void* cuda_stream) {
+    Elem* e = elem_at(c, elem);
+    if (!e || !R || !Z || !S || !A) return fail(c, SS_EINVAL, "bad element or NULL array");
+    if (!c->have_params) return fail(c, SS_ESTATE, "ss_set_params must precede ss_set_state_dev");
+    const cudaStream_t user = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+    int rc = order_streams(c, user, c->stream);
+    if (rc != SS_OK) return rc;
+    rc = stage_at_least(c, sizeof(int));
+    if (rc != SS_OK) return rc;
+    int* dF = static_cast<int*>(c->stage);
+    rc = c->prec == SS_FP64 ? check_convert_state<double>(c, *e, R, A, S, Z, dF)
+                            : check_convert_state<float>(c, *e, R, A, S, Z, dF);
+    if (rc != SS_OK) return rc;
+    if (!c->initialized) {
+        for (int i = 0; i < (int)c->el.size(); ++i) {
+            if (i == elem) continue;
+            rc = c->prec == SS_FP64 ? launch_init<double>(c, c->el[i]) : launch_init<float>(c, c->el[i]);
+            if (rc != SS_OK) return rc;
+        }
+        c->initialized = true;
+    }
+    return SS_OK;
+}
+
+int ss_zhist(ss_ctx* c, int elem, int64_t* hist, int cap, int* n_out) {
+    Elem* e = elem_at(c, elem);
+    if (!e || !n_out || cap < 0) return fail(c, SS_EINVAL, "bad element, NULL n_out or negative cap");
+    if (!c->have_params) return fail(c, SS_ESTATE, "no parameters");
+    const int nb = e->zmax + 1;
+    *n_out = nb;
+    if (!hist || cap == 0) return SS_OK;
+    if (!c->initialized) return fail(c, SS_ESTATE, "no state yet: ss_run or ss_set_state first");
+    int rc = stage_at_least(c, (size_t)(nb + 1) * sizeof(unsigned long long));
+    if (rc != SS_OK) return rc;
+    unsigned long long* dh = static_cast<unsigned long long*>(c->stage);
+    SS_CUDA(c, cudaMemsetAsync(dh, 0, (size_t)(nb + 1) * sizeof(unsigned long long), c->stream));
+    const int blocks = std::max(1, std::min((e->M + 255) / 256, 1024));
+    ssk::zhist_kernel<<<blocks, 256, 0, c->stream>>>(e->Z, e->M, nb, dh);
+    SS_CUDA(c, cudaGetLastError());
+    c->launches++;
+    std::vector<unsigned long long> h(nb + 1);
+    SS_CUDA(c, cudaMemcpyAsync(h.data(), dh, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               c->stream));
+    SS_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int z = 0; z < std::min(cap, nb); ++z) hist[z] = (int64_t)h[z];
+    if (h[nb] != 0) return fail(c, SS_EOVERFLOW, "a chain's Z is outside 0..z_max (see ss_status)");
     return SS_OK;
 }
 
@@ -1712,6 +1806,15 @@ __global__ void noalloc_reduce_kernel(const double* acc64, int slices, int L, do
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The velocity gradient of a call, by value: the launch copies it into the
+// scratch array, so nothing on the device reads caller or stack memory later.
+struct KappaVal {
+    double k[9];
+};
+__global__ void noalloc_put_kappa_kernel(const KappaVal kv, double* __restrict__ dst) {
+    if (threadIdx.x < 9) dst[threadIdx.x] = kv.k[threadIdx.x];
+}
+
 template <typename T, int W, int B>
 int noalloc_launches(ss_ctx* c, const ss_params& p, int M, int N, int zmax, uint32_t chain_base, int64_t t0,
                      int64_t n_steps, void* R, void* A, int32_t* S, int32_t* Z, unsigned char* scr,
@@ -1871,12 +1974,10 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     // what must start at zero: history, sums, counters, status (not the series)
     if (cudaMemsetAsync(scr, 0, off_ser, st) != cudaSuccess) return SS_ECUDA;
-    double kap_h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (kappa) std::memcpy(kap_h, kappa, sizeof(kap_h));
-    // a copy from pageable host memory is staged before cudaMemcpyAsync returns,
-    // so kap_h may go out of scope afterwards
-    if (cudaMemcpyAsync(scr + off_kap, kap_h, sizeof(kap_h), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return SS_ECUDA;
+    KappaVal kv{};
+    if (kappa) std::memcpy(kv.k, kappa, sizeof(kv.k));
+    noalloc_put_kappa_kernel<<<1, 32, 0, st>>>(kv, reinterpret_cast<double*>(scr + off_kap));
+    if (cudaGetLastError() != cudaSuccess) return SS_ECUDA;
     const int zm = c.el[0].zmax;
 #define SS_NOALLOC_ARGS                                                                                          \
     &c, c.P, n_chains, n_beads, zm, chain_base, t0, n_steps, R, A, S, Z, scr, off_hist, off_ser, off_lev,       \

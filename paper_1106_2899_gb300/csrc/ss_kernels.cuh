@@ -529,10 +529,10 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     unsigned cnt_up = 0, cnt_dn = 0, cnt_cr = 0, cnt_de = 0, cnt_drop = 0;
 
     // slot table: the spring vector d_j = R_{S_j} - A_j of every occupied slot
-    // j, written at the end of each step for the next step's spring forces
-    // (d_j does not change when a chain and its anchors are shifted together,
-    // so recentring leaves it valid); the re-indexing below also uses it as
-    // scratch.  Record NP is zero: an empty slot mask reads it.
+    // j, written at the end of each step for the next step's spring forces; a
+    // recentring step rewrites it from the shifted coordinates, as a launch
+    // computes it here at its start.  The re-indexing below also uses the
+    // table as scratch.  Record NP is zero: an empty slot mask reads it.
     __syncwarp();  // positions of this warp's chains are in the table
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -1415,6 +1415,47 @@ __global__ void state_convert_kernel(const double* __restrict__ Rh, const double
         A[((size_t)m * 3 + d) * NP + i] = i < z ? T(Ah[((size_t)m * zm + i) * 3 + d]) : T(0);
     }
     S[(size_t)m * NP + i] = i < z ? Sh[(size_t)m * zm + i] : -1;
+}
+
+// The state in the caller's layout (R [M][N][3], A [M][zm][3] double; S
+// [M][zm] int32 with -1 for empty slots, Z [M]) from the device layout, into
+// caller-owned device arrays (any may be null).  One thread per (chain, i).
+template <typename T>
+__global__ void state_export_kernel(const T* __restrict__ R, const T* __restrict__ A, const int32_t* __restrict__ S,
+                                    const int32_t* __restrict__ Z, int M, int N, int zm, int NP, double* __restrict__ Ro,
+                                    double* __restrict__ Ao, int32_t* __restrict__ So, int32_t* __restrict__ Zo) {
+    const int width = N > zm ? N : zm;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)M * width) return;
+    const int m = (int)(id / width), i = (int)(id % width);
+    const int z = Z[m];
+    if (i == 0 && Zo) Zo[m] = z;
+    if (i < N && Ro)
+        for (int d = 0; d < 3; ++d) Ro[((size_t)m * N + i) * 3 + d] = (double)R[((size_t)m * 3 + d) * NP + i];
+    if (i < zm) {
+        const bool occ = i < z;
+        if (So) So[(size_t)m * zm + i] = occ ? S[(size_t)m * NP + i] : -1;
+        if (Ao)
+            for (int d = 0; d < 3; ++d)
+                Ao[((size_t)m * zm + i) * 3 + d] = occ ? (double)A[((size_t)m * 3 + d) * NP + i] : 0.0;
+    }
+}
+
+// Histogram of the slip-spring numbers Z of M chains: hist[z] += number of
+// chains with Z = z, z = 0..nb-1 (nb <= kMaxSlots + 1), bins per CTA in shared
+// memory.  A Z outside 0..nb-1 (never produced by the step) is counted in bin
+// nb, the overflow bin.
+__global__ void zhist_kernel(const int32_t* __restrict__ Z, int M, int nb, unsigned long long* __restrict__ hist) {
+    __shared__ unsigned int h[kMaxSlots + 2];
+    for (int i = threadIdx.x; i <= nb; i += blockDim.x) h[i] = 0u;
+    __syncthreads();
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const int z = Z[m];
+        atomicAdd(&h[(z >= 0 && z < nb) ? z : nb], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= nb; i += blockDim.x)
+        if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
 }
 
 // Correlator group sums from the slice sums: out[g][l][lag][ch][d] (the layout

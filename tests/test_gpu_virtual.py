@@ -3,7 +3,7 @@
 * Channel TT (later and origin both sigma + sigma^(v)) in FP64 equals the
   oracle's sums on the same chains and random numbers; enabling it leaves the
   AUTO and TOTAL sums bit for bit unchanged.
-* The relative virtual-stress contribution of Sec. 4.2 (Eq.
+* The relative virtual-stress contribution of Sec. 4.1 (Eq.
   relative_contribution_virtual_stress_to_shear_relaxation_modulus),
   VIRTUAL / TOTAL with VIRTUAL = TT - TOTAL, at N = 40: the paper reports it
   as roughly 25% and not strongly time dependent; printed numbers of the paper

@@ -59,7 +59,7 @@ def test_multitau_streaming_equals_batch_definition(T):
 @pytest.mark.parametrize("T", [33, 1000])
 def test_multitau_tt_channel_equals_batch_definition(T):
     """Channel TT (later and origin both sigma + sigma_v, the numerator of the
-    virtual-stress share of Sec. 4.2 minus TOTAL): the batch definition applied
+    virtual-stress share of Sec. 4.1 minus TOTAL): the batch definition applied
     to the series whose sigma columns are the sigma + sigma_v columns."""
     rng = np.random.default_rng(T + 7)
     x = rng.normal(size=(T, 6)) + 0.2

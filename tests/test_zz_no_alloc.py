@@ -1,14 +1,16 @@
 """The allocation-free entry point ss_run_noalloc against the context API.
 
-ss_run_noalloc serves callers that cannot call cudaMalloc (graph capture in
-progress, a host that owns device memory through its own pool, real-time
-loops).  Its kernel scratch lives in one file-scope device array; the caller
-passes the state and the outputs.  This test drives it through the C ABI on
-caller-owned device buffers and checks two calls in a row against ss_run on a
-context started from the same state: integers equal, positions within the
-parity tolerances (1e-10 in FP64, 1e-4 relative in FP32), correlator sums of
-each call within 1e-9 relative.  The file is named so that pytest collects it
-last.
+ss_run_noalloc serves callers that cannot call cudaMalloc: a host that owns
+all device memory through its own pool, a framework with a device memory
+budget fixed at start-up, real-time loops in which an allocation could block.
+Its kernel scratch lives in one file-scope device array; the caller passes the
+state and the outputs.  This test drives it through the C ABI on caller-owned
+device buffers and checks two calls in a row against ss_run on a context
+started from the same state: integers equal, positions within the parity
+tolerances (1e-10 in FP64, 1e-4 relative in FP32), correlator sums of each
+call within 1e-9 relative.  One case runs under simple shear (the velocity
+gradient set from step 0 on the context, passed to each allocation-free call).
+The file is named so that pytest collects it last.
 """
 import ctypes as C
 
@@ -52,16 +54,24 @@ def _from_device_layout(R, A, S, Z, N, zm):
     return out
 
 
-def _noalloc_call(lib, params, precision, seed, M, N, t0, n, dev, corr, status, stream):
+def _noalloc_call(lib, params, precision, seed, M, N, t0, n, dev, corr, status, stream, kappa=None):
     R, A, S, Z = dev
-    rc = lib.ss_run_noalloc(C.byref(params), precision, seed, M, N, 0, t0, n, None, C.c_void_p(R.data_ptr()),
+    kap = None
+    if kappa is not None:
+        # a fresh host array per call, released right after it: the call must
+        # not keep reading it
+        kap = np.ascontiguousarray(kappa, dtype=np.float64).reshape(9).copy()
+    rc = lib.ss_run_noalloc(C.byref(params), precision, seed, M, N, 0, t0, n,
+                            kap.ctypes.data_as(C.POINTER(C.c_double)) if kap is not None else None,
+                            C.c_void_p(R.data_ptr()),
                             C.c_void_p(A.data_ptr()), C.c_void_p(S.data_ptr()), C.c_void_p(Z.data_ptr()),
                             C.c_void_p(corr.data_ptr()), C.c_void_p(status.data_ptr()), C.c_void_p(stream))
     assert rc == 0, nat.ERRORS.get(rc, rc)
 
 
-@pytest.mark.parametrize("precision,N", [("fp64", 16), ("fp32", 32), ("fp32", 80)])
-def test_noalloc_two_calls_match_context(cuda_ok, precision, N):
+@pytest.mark.parametrize("precision,N,gdot", [("fp64", 16, 0.0), ("fp32", 32, 0.0), ("fp32", 80, 0.0),
+                                             ("fp32", 32, 0.05), ("fp64", 24, 0.05)])
+def test_noalloc_two_calls_match_context(cuda_ok, precision, N, gdot):
     import torch
 
     from paper_1106_2899_gb300 import build
@@ -75,9 +85,12 @@ def test_noalloc_two_calls_match_context(cuda_ok, precision, N):
     dtype = np.float64 if precision == "fp64" else np.float32
 
     # the existing entry points, on a context
+    kappa = synth.shear_kappa(gdot) if gdot else None
     g = SlipSpring([(M, N)], precision=precision, seed=seed)
     g.set_params(**kw)
     g.set_state(st0)
+    if kappa is not None:
+        g.set_flow(kappa, from_step=0)
     g.run(n1)
     ref1, acc1 = g.get_state(), g.corr_sums()[0].sum(axis=0)
     g.reset_observables()
@@ -96,7 +109,7 @@ def test_noalloc_two_calls_match_context(cuda_ok, precision, N):
     lags = np.array([[(k << l) if (l == 0 or k >= 8) else -1 for k in range(16)] for l in range(levels)])
     rtol = 1e-10 if precision == "fp64" else 1e-4
     for call, (t0, n, ref, acc) in enumerate([(0, n1, ref1, acc1), (n1, n2, ref2, acc2)]):
-        _noalloc_call(lib, params, prec, seed, M, N, t0, n, dev, corr, status, stream)
+        _noalloc_call(lib, params, prec, seed, M, N, t0, n, dev, corr, status, stream, kappa)
         torch.cuda.synchronize()
         got = _from_device_layout(*[x.cpu().numpy() for x in dev], N, zm)
         assert int(status.item()) == 0
