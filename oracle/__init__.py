@@ -9,6 +9,7 @@ docstring in oracle.py and each comment in ss_oracle.c names its pin).
 """
 from .oracle import (  # noqa: F401
     CORR_P,
+    OPS_CATEGORIES,
     Ensemble,
     Params,
     corr_counts,
@@ -17,6 +18,7 @@ from .oracle import (  # noqa: F401
     decode_block,
     init_chain,
     norm_ppf,
+    op_counts,
     philox,
     step_chain,
     stress,

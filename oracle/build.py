@@ -42,5 +42,21 @@ def build(force: bool = False) -> str:
     return compile_oracle(SRC, LIB)
 
 
+COUNT_LIB = os.path.join(OUT_DIR, "libssoracle_ops.so")
+
+
+def build_counting(force: bool = False) -> str:
+    """The single-threaded operation-counting build (-DOR_COUNT_OPS, no OpenMP)."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    if not force and os.path.exists(COUNT_LIB) and os.path.getmtime(COUNT_LIB) >= newest:
+        return COUNT_LIB
+    tmp = COUNT_LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-Wall", "-Wextra", "-DOR_COUNT_OPS", "-o", tmp, SRC, "-lm"])
+    os.replace(tmp, COUNT_LIB)
+    return COUNT_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))

@@ -22,7 +22,7 @@ class _CParams(C.Structure):
                 ("destroy_new", C.c_int), ("N0", C.c_double), ("Ns", C.c_double),
                 ("zeta_s", C.c_double), ("dt", C.c_double), ("b", C.c_double),
                 ("kT", C.c_double), ("zeta", C.c_double), ("k_b", C.c_double),
-                ("k_s", C.c_double)]
+                ("k_s", C.c_double), ("integrator", C.c_int)]
 
 
 class _CChain(C.Structure):
@@ -35,12 +35,27 @@ class _CInfo(C.Structure):
                 ("created", C.c_int), ("destroyed", C.c_int), ("dropped", C.c_int)]
 
 
+OPS_CATEGORIES = ["philox", "decode", "bond", "spring", "euler", "advect", "hop", "create", "destroy", "stress",
+                  "correlator"]
+_count_lib = None
+
+
 def _load():
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build()
-    lib = C.CDLL(path)
+    _lib = _configure(C.CDLL(_build.build()))
+    return _lib
+
+
+def _load_counting():
+    global _count_lib
+    if _count_lib is None:
+        _count_lib = _configure(C.CDLL(_build.build_counting()))
+    return _count_lib
+
+
+def _configure(lib):
     P = C.POINTER
     dp, ip, lp = P(C.c_double), P(C.c_int32), P(C.c_int64)
     u32p = P(C.c_uint32)
@@ -79,7 +94,12 @@ def _load():
     lib.or_corr_series_tt.restype = None
     lib.or_ens_corr_tt.argtypes = [C.c_void_p, dp]
     lib.or_ens_corr_tt.restype = None
-    _lib = lib
+    lib.or_ops_get.argtypes = [lp]
+    lib.or_ops_get.restype = None
+    lib.or_ops_reset.argtypes = []
+    lib.or_ops_reset.restype = None
+    lib.or_ops_enabled.argtypes = []
+    lib.or_ops_enabled.restype = C.c_int
     return lib
 
 
@@ -104,11 +124,12 @@ class Params:
     zeta: float = 1.0
     k_b: float = 0.0          # 0 -> 3 kT / b^2
     k_s: float = 0.0          # 0 -> 3 kT / (Ns b^2)
+    integrator: int = 0       # 0: Euler-Maruyama (Sec. 3.1); 1: stochastic Heun (second-order SRK)
 
     def c(self):
         zm = self.z_max if self.z_max > 0 else self.N
         p = _CParams(self.N, zm, self.create_mode, self.destroy_new, self.N0, self.Ns,
-                     self.zeta_s, self.dt, self.b, self.kT, self.zeta, self.k_b, self.k_s)
+                     self.zeta_s, self.dt, self.b, self.kT, self.zeta, self.k_b, self.k_s, self.integrator)
         _load().or_params_derive(C.byref(p))
         return p
 
@@ -207,11 +228,12 @@ def stress(p: Params, state):
 
 class Ensemble:
     """M independent chains run by the oracle, with the same calls as the library:
-    init, set_flow, run, get/set_state, correlator sums, stress logs."""
+    init, set_flow, run, get/set_state, correlator sums, stress logs.
+    counting=True uses the operation-counting build (single-threaded)."""
 
     def __init__(self, p: Params, seed: int, M: int, chain_offset: int = 0, groups: int = 1,
-                 levels: int = 24, log_every: int = 0, max_logs: int = 0):
-        self.lib = _load()
+                 levels: int = 24, log_every: int = 0, max_logs: int = 0, counting: bool = False):
+        self.lib = _load_counting() if counting else _load()
         self.p = p
         self.M, self.G, self.levels = M, groups, levels
         self.N, self.zm = p.N, p.zm
@@ -314,6 +336,27 @@ class Ensemble:
         out = np.zeros(5, dtype=np.int64)
         self.lib.or_ens_counters(self.h, _ptr(out, C.c_int64))
         return dict(zip(["hops_up", "hops_down", "created", "destroyed", "dropped"], out.tolist()))
+
+
+def op_counts(p: Params, seed: int, M: int, steps: int, levels: int = 24, warm: int = 200, kappa=None,
+              log_every: int = 0):
+    """Operations of the method per bead-step, by substep (ss_oracle.h states the
+    counting rules), from the counting build of the oracle run single-threaded
+    on M chains for `steps` steps after `warm` steps of warm-up."""
+    e = Ensemble(p, seed=seed, M=M, levels=levels, log_every=log_every,
+                 max_logs=(warm + steps) // log_every + 1 if log_every else 0, counting=True)
+    lib = e.lib
+    assert lib.or_ops_enabled() == 1
+    e.init()
+    if kappa is not None:
+        e.set_flow(0, kappa)
+    e.run(warm, nthreads=1)
+    lib.or_ops_reset()
+    e.run(steps, nthreads=1)
+    out = np.zeros(len(OPS_CATEGORIES), dtype=np.int64)
+    lib.or_ops_get(_ptr(out, C.c_int64))
+    per = out / float(M * p.N * steps)
+    return dict(zip(OPS_CATEGORIES, per.tolist()))
 
 
 def corr_series(x, levels: int, tt: bool = False):

@@ -26,6 +26,23 @@
 #include <omp.h>
 #endif
 
+/* ------------------------------------------------------ operation counts --
+ * With -DOR_COUNT_OPS (a separate, single-threaded build) every executed
+ * operation of the method adds to a counter of its substep; the rules are in
+ * ss_oracle.h.  Without it OR_OPS compiles to nothing. */
+#ifdef OR_COUNT_OPS
+static int64_t or_ops[OR_OPC_N];
+#define OR_OPS(cat, n) (or_ops[(cat)] += (int64_t)(n))
+void or_ops_get(int64_t out[OR_OPC_N]) { memcpy(out, or_ops, sizeof(or_ops)); }
+void or_ops_reset(void) { memset(or_ops, 0, sizeof(or_ops)); }
+int or_ops_enabled(void) { return 1; }
+#else
+#define OR_OPS(cat, n) ((void)0)
+void or_ops_get(int64_t out[OR_OPC_N]) { memset(out, 0, sizeof(int64_t) * OR_OPC_N); }
+void or_ops_reset(void) {}
+int or_ops_enabled(void) { return 0; }
+#endif
+
 /* ---------------------------------------------------------------- Philox -- */
 /* Philox4x32-10 as published by Salmon et al., SC'11: a 4x32-bit counter and a
  * 2x32-bit key; each round multiplies counter words 0 and 2 by two fixed odd
@@ -41,6 +58,7 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
     uint32_t k0 = key[0], k1 = key[1];
     for (int round = 0; round < 10; ++round) {
+        OR_OPS(OR_OPC_PHILOX, round > 0 ? 6 : 4);
         if (round > 0) {
             k0 += OR_PHILOX_W0;
             k1 += OR_PHILOX_W1;
@@ -76,6 +94,9 @@ static const double OR_PI = 3.14159265358979323846;
 
 /* Box-Muller: radius sqrt(-2 ln v), v in (0,1]; angle pi*(2u-1), u in [0,1). */
 static void or_box_muller(uint32_t wa, uint32_t wb, double* n_cos, double* n_sin) {
+    /* shift, +1, convert, scale, log, x(-2), sqrt; shift, convert, scale,
+     * 2u - 1 (fused), x pi, cos, sin, two products */
+    OR_OPS(OR_OPC_DECODE, 16);
     double v = ((double)(wa >> 8) + 1.0) * OR_TWO_M24;
     double u = (double)(wb >> 8) * OR_TWO_M24;
     double r = sqrt(-2.0 * log(v));
@@ -89,6 +110,7 @@ void or_decode_block(const uint32_t w[4], double n[4], double* u) {
     or_box_muller(w[2], w[3], &n[2], &n[3]);
     uint32_t lo = (w[0] & 0xFFu) | ((w[1] & 0xFFu) << 8) | ((w[2] & 0xFFu) << 16);
     *u = (double)lo * OR_TWO_M24;
+    OR_OPS(OR_OPC_DECODE, 9); /* three masks, two shifts, two ors, convert, scale */
 }
 
 /* ------------------------------------------------------------ parameters -- */
@@ -179,6 +201,8 @@ static double or_dist2(const double x[3], const double y[3]) {
  * evaluated as 2/(1+exp(2y)), the same number without cancellation; y is
  * clamped to [-40, 40] where the expression is saturated anyway. */
 static double or_hop_prob(const or_params* p, double d_new, double d_old) {
+    /* difference, scale, 2 clamps, x2, exp, +1, reciprocal, x(2 pref), cap */
+    OR_OPS(OR_OPC_HOP, 10);
     double y = p->k_s * (d_new - d_old) / (4.0 * p->kT);
     if (y > 40.0) y = 40.0;
     if (y < -40.0) y = -40.0;
@@ -223,35 +247,81 @@ void or_step_chain_tape(const or_params* p, const uint32_t key[2], uint32_t chai
             if (i > 0) f += p->k_b * (c->R[i - 1][a] - c->R[i][a]);
             if (i + 1 < N) f += p->k_b * (c->R[i + 1][a] - c->R[i][a]);
             F[i][a] = f;
+            OR_OPS(OR_OPC_BOND, 2 * ((i > 0) + (i + 1 < N))); /* difference, multiply-add */
         }
     for (int j = 0; j < c->Z; ++j) {
         int s = c->S[j];
         for (int a = 0; a < 3; ++a) F[s][a] += p->k_s * (c->A[j][a] - c->R[s][a]);
+        OR_OPS(OR_OPC_SPRING, 6);
     }
     const double mob = p->dt / p->zeta;
     const double amp = sqrt(2.0 * p->kT * p->dt / p->zeta);
     double Rn[OR_NMAX][3];
+    int kap_on = 0; /* the flow term of the method vanishes when kappa = 0 */
+    for (int k = 0; k < 9; ++k) kap_on |= kap[k] != 0.0;
+    OR_OPS(OR_OPC_EULER, (int64_t)N * (kap_on ? 6 + 9 : 6)); /* 2 multiply-adds (+3 flow, +1) per component */
+    if (kap_on) OR_OPS(OR_OPC_ADVECT, (int64_t)c->Z * 12); /* kappa . A: 3, A + dt flow: 1 per component */
+    double flowR[OR_NMAX][3], flowA[OR_NMAX][3];
     for (int i = 0; i < N; ++i)
         for (int a = 0; a < 3; ++a) {
             double flow = kap[3 * a + 0] * c->R[i][0] + kap[3 * a + 1] * c->R[i][1] +
                           kap[3 * a + 2] * c->R[i][2];
+            flowR[i][a] = flow;
             Rn[i][a] = c->R[i][a] + mob * F[i][a] + p->dt * flow + amp * nrm[i][a];
         }
-    for (int j = 0; j < c->Z; ++j) {
-        double An[3];
+    double An[OR_NMAX][3];
+    for (int j = 0; j < c->Z; ++j)
         for (int a = 0; a < 3; ++a) {
             double flow = kap[3 * a + 0] * c->A[j][0] + kap[3 * a + 1] * c->A[j][1] +
                           kap[3 * a + 2] * c->A[j][2];
-            An[a] = c->A[j][a] + p->dt * flow;
+            flowA[j][a] = flow;
+            An[j][a] = c->A[j][a] + p->dt * flow;
         }
-        for (int a = 0; a < 3; ++a) c->A[j][a] = An[a];
+    if (p->integrator == OR_HEUN) {
+        /* corrector: drifts at the predicted state (Rn, An) with the same
+         * springs, then the average of both drifts and the same noise */
+        double F2[OR_NMAX][3];
+        for (int i = 0; i < N; ++i)
+            for (int a = 0; a < 3; ++a) {
+                double f = 0.0;
+                if (i > 0) f += p->k_b * (Rn[i - 1][a] - Rn[i][a]);
+                if (i + 1 < N) f += p->k_b * (Rn[i + 1][a] - Rn[i][a]);
+                F2[i][a] = f;
+                OR_OPS(OR_OPC_BOND, 2 * ((i > 0) + (i + 1 < N)));
+            }
+        for (int j = 0; j < c->Z; ++j) {
+            int s = c->S[j];
+            for (int a = 0; a < 3; ++a) F2[s][a] += p->k_s * (An[j][a] - Rn[s][a]);
+            OR_OPS(OR_OPC_SPRING, 6);
+        }
+        const double hmob = 0.5 * mob, hdt = 0.5 * p->dt;
+        OR_OPS(OR_OPC_EULER, (int64_t)N * (kap_on ? 9 + 9 : 9)); /* sum of forces, 2 multiply-adds, noise */
+        if (kap_on) OR_OPS(OR_OPC_ADVECT, (int64_t)c->Z * 12);
+        for (int i = 0; i < N; ++i) {
+            double flow2[3];
+            for (int a = 0; a < 3; ++a)
+                flow2[a] = kap[3 * a + 0] * Rn[i][0] + kap[3 * a + 1] * Rn[i][1] + kap[3 * a + 2] * Rn[i][2];
+            for (int a = 0; a < 3; ++a)
+                Rn[i][a] = c->R[i][a] + hmob * (F[i][a] + F2[i][a]) + hdt * (flowR[i][a] + flow2[a]) +
+                           amp * nrm[i][a];
+        }
+        for (int j = 0; j < c->Z; ++j) {
+            double flow2[3];
+            for (int a = 0; a < 3; ++a)
+                flow2[a] = kap[3 * a + 0] * An[j][0] + kap[3 * a + 1] * An[j][1] + kap[3 * a + 2] * An[j][2];
+            for (int a = 0; a < 3; ++a) An[j][a] = c->A[j][a] + hdt * (flowA[j][a] + flow2[a]);
+        }
     }
+    for (int j = 0; j < c->Z; ++j) memcpy(c->A[j], An[j], sizeof(double) * 3);
     memcpy(c->R, Rn, sizeof(double) * 3 * (size_t)N);
 
     /* ---- substep 2: hops on the post-substep-1 positions.  One uniform per
      * spring: [0, p+) -> S+1, [p+, p+ + p-) -> S-1, otherwise stay. */
     for (int j = 0; j < c->Z; ++j) {
         int s = c->S[j];
+        /* three squared distances (3 differences, 3 products/multiply-adds
+         * each), the decision: p+ + p-, two comparisons */
+        OR_OPS(OR_OPC_HOP, 6 * (1 + (s < N - 1) + (s > 0)) + 3);
         double d0 = or_dist2(c->R[s], c->A[j]);
         double pp = (s < N - 1) ? or_hop_prob(p, or_dist2(c->R[s + 1], c->A[j]), d0) : 0.0;
         double pm = (s > 0) ? or_hop_prob(p, or_dist2(c->R[s - 1], c->A[j]), d0) : 0.0;
@@ -290,6 +360,7 @@ void or_step_chain_tape(const or_params* p, const uint32_t key[2], uint32_t chai
         double sa = sqrt(p->kT / p->k_s);
         for (int j = first; j < last; ++j) {
             double u = uni[j];
+            OR_OPS(OR_OPC_CREATE, 2); /* u < pc, u < 2 pc */
             or_margin(&inf.min_margin, u, pc);
             or_margin(&inf.min_margin, u, 2.0 * pc);
             int end = -1;
@@ -305,6 +376,7 @@ void or_step_chain_tape(const or_params* p, const uint32_t key[2], uint32_t chai
             or_block(key, (uint32_t)j, step, OR_PURPOSE_CREATE, chain_id, w);
             or_decode_block(w, n, &uu);
             new_end[j] = end;
+            OR_OPS(OR_OPC_CREATE, 3); /* anchor: one multiply-add per component */
             for (int a = 0; a < 3; ++a) new_A[j][a] = c->R[end][a] + sa * n[a];
             inf.created++;
         }
@@ -318,6 +390,7 @@ void or_step_chain_tape(const or_params* p, const uint32_t key[2], uint32_t chai
         alive[j] = 1;
         int s = c->S[j];
         if (s == 0 || s == N - 1) {
+            OR_OPS(OR_OPC_DESTROY, 1);
             or_margin(&inf.min_margin, nrm[j][3], cd);
             int kill = nrm[j][3] < cd;
             if (replay) kill = (replay[j] & 16) != 0;
@@ -330,6 +403,7 @@ void or_step_chain_tape(const or_params* p, const uint32_t key[2], uint32_t chai
     }
     for (int j = first; j < last; ++j) {
         if (new_end[j] < 0 || !p->destroy_new) continue;
+        OR_OPS(OR_OPC_DESTROY, 1);
         or_margin(&inf.min_margin, nrm[j][3], cd);
         int kill = nrm[j][3] < cd;
         if (replay) kill = (replay[j] & 32) != 0;
@@ -417,6 +491,7 @@ static void or_corr_push(or_corr_chain* cc, double* acc /* [levels][P][2][3] */,
     for (int k = kmin; k < OR_P; ++k) {
         if (cc->nfill[l] <= k) break;
         double* a = acc + ((size_t)l * OR_P + (size_t)k) * 6;
+        OR_OPS(OR_OPC_CORR, 6); /* one multiply-add per product (the optional channel TT not counted) */
         for (int c = 0; c < 3; ++c) {
             a[c] += v[c] * cc->hist[l][k][c];
             a[3 + c] += v[c] * cc->hist[l][k][3 + c];
@@ -428,7 +503,9 @@ static void or_corr_push(or_corr_chain* cc, double* acc /* [levels][P][2][3] */,
     }
     for (int s = 0; s < 6; ++s) cc->pend[l][s] += v[s];
     cc->npend[l]++;
+    OR_OPS(OR_OPC_CORR, 6); /* block sums */
     if (cc->npend[l] == 2) {
+        OR_OPS(OR_OPC_CORR, 6); /* block means */
         double up[6];
         for (int s = 0; s < 6; ++s) up[s] = 0.5 * cc->pend[l][s];
         memset(cc->pend[l], 0, sizeof(cc->pend[l]));
@@ -476,6 +553,7 @@ or_ens* or_ens_create(const or_params* p, uint64_t seed, int M, uint32_t chain_o
                       int levels, int log_every, int max_logs) {
     if (M <= 0 || G <= 0 || G > M || levels < 1 || levels > OR_LMAX) return NULL;
     if (p->N < 2 || p->N > OR_NMAX || p->z_max < 1 || p->z_max > p->N) return NULL;
+    if (p->integrator != OR_EULER && p->integrator != OR_HEUN) return NULL;
     or_ens* e = (or_ens*)calloc(1, sizeof(or_ens));
     e->p = *p;
     or_params_derive(&e->p);
@@ -561,6 +639,8 @@ int or_ens_run_tape(or_ens* e, int64_t n_steps, int nthreads, int32_t* Z_tr, int
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : cnt[:5])
+#else
+    (void)nthreads;
 #endif
     for (int g = 0; g < G; ++g) {
         int m0 = (int)(((int64_t)g * M) / G), m1 = (int)(((int64_t)(g + 1) * M) / G);
@@ -582,6 +662,13 @@ int or_ens_run_tape(or_ens* e, int64_t n_steps, int nthreads, int32_t* Z_tr, int
                 cnt[4] += info.dropped;
                 double sig[9], sigv[9];
                 or_stress(&e->p, c, sig, sigv);
+                /* the correlator needs the off-diagonal xy, xz, yz of sigma and
+                 * sigma + sigma_v: per bond or spring 3 differences, 2 products,
+                 * 3 multiply-adds; 3 additions per chain.  A log step adds the
+                 * diagonal (3 multiply-adds per bond and spring, 3 subtractions). */
+                OR_OPS(OR_OPC_STRESS, 8 * (int64_t)(e->p.N - 1 + c->Z) + 3);
+                if (e->log_every > 0 && (t + 1) % e->log_every == 0)
+                    OR_OPS(OR_OPC_STRESS, 3 * (int64_t)(e->p.N - 1 + c->Z) + 6);
                 double v[6] = {sig[1], sig[2], sig[5], sig[1] + sigv[1], sig[2] + sigv[2], sig[5] + sigv[5]};
                 or_corr_push(cc, acc, e->acc_tt + (size_t)g * e->levels * OR_P * 3, e->levels, 0, v);
                 if (e->log_every > 0 && (t + 1) % e->log_every == 0) {

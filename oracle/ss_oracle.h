@@ -55,7 +55,20 @@ typedef struct {
     double dt;       /* time step                                                */
     double b, kT, zeta;
     double k_b, k_s;
+    int integrator; /* OR_EULER (the paper's scheme, Sec. 3.1) or OR_HEUN        */
 } or_params;
+
+/* Integrators of the bead/anchor substep (substep 1 of Sec. 3.1).  OR_HEUN is
+ * the stochastic Heun scheme, the second-order stochastic Runge-Kutta method
+ * for additive noise that Sec. 3.1 names as the more accurate alternative
+ * (Honeycutt 1992): the Euler step is the predictor; the corrector adds half
+ * the drift at the start and half the drift at the predicted state, with the
+ * same noise.  Slip-spring indices and anchors of the step enter both drifts
+ * (anchors at their predicted positions under a flow).  Hops, creation and
+ * destruction are unchanged.  Pinned by the exact discrete Rouse closed form
+ * of the scheme (per mode r = 1 - x + x^2/2 and variance scale (1 - x/2)^2,
+ * x = dt k_b mu_p/zeta), whose stationary bias is second order in dt. */
+enum { OR_EULER = 0, OR_HEUN = 1 };
 
 /* Fill k_b, k_s from b, Ns, kT where they are <= 0. */
 void or_params_derive(or_params* p);
@@ -129,6 +142,38 @@ void or_corr_series(const double* x, int64_t T, int levels, double* acc);
 /* The same, also accumulating channel TT (later sigma + sigma_v times origin
  * sigma + sigma_v) into acc_tt[levels][OR_P][3] when acc_tt is not NULL. */
 void or_corr_series_tt(const double* x, int64_t T, int levels, double* acc, double* acc_tt);
+
+/* ---- operation counts (test infrastructure) -------------------------------
+ * Built with -DOR_COUNT_OPS (single-threaded runs only), the oracle counts the
+ * operations of the method it executes, by substep.  Rules: one operation per
+ * arithmetic operator, comparison, integer shift/mask/logic operator and
+ * int-to-float conversion; a library call (log, sqrt, sin, cos, exp) or a
+ * reciprocal one; a product added in the same expression counts once with the
+ * addition (a fused multiply-add); a 32x32 -> 64-bit product with both halves
+ * once; a three-input xor once; constants of the parameters (dt kT/zeta_s,
+ * k_s/(4 kT), ...) are formed once and not counted per use.  The velocity-
+ * gradient terms count only when kappa is not zero.  The stress counts what
+ * the outputs use (off-diagonal components every step, the diagonal at log
+ * steps).  Loads, stores, index arithmetic, control flow and the test-support
+ * bookkeeping (decision margins, traces, tapes) are not counted.  Without the
+ * flag or_ops_get returns zeros and or_ops_enabled 0. */
+enum {
+    OR_OPC_PHILOX = 0, /* Philox4x32-10 blocks                             */
+    OR_OPC_DECODE,     /* Box-Muller pairs and the 24-bit uniform          */
+    OR_OPC_BOND,       /* bond forces                                      */
+    OR_OPC_SPRING,     /* slip-spring forces                               */
+    OR_OPC_EULER,      /* Euler-Maruyama update (with the flow term)       */
+    OR_OPC_ADVECT,     /* affine anchor advection                          */
+    OR_OPC_HOP,        /* hop probabilities and decisions                  */
+    OR_OPC_CREATE,     /* creation attempts and new anchors                */
+    OR_OPC_DESTROY,    /* destruction tests                                */
+    OR_OPC_STRESS,     /* stress and virtual stress                        */
+    OR_OPC_CORR,       /* multiple-tau correlator                          */
+    OR_OPC_N
+};
+void or_ops_get(int64_t out[OR_OPC_N]);
+void or_ops_reset(void);
+int or_ops_enabled(void);
 
 /* ---- ensemble runner (mirrors the library's calls) ----------------------- */
 typedef struct or_ens or_ens;

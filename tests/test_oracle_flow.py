@@ -116,7 +116,7 @@ def test_flow_schedule_switches_exactly_at_from_step():
         assert np.allclose(st["A"][occ], wantA[occ], rtol=1e-13, atol=1e-13 * np.abs(wantA).max()), n
 
 
-def sheared_rouse_stress(N, k_b, dt, zeta, kT, kappa):
+def sheared_rouse_stress(N, k_b, dt, zeta, kT, kappa, scheme="euler"):
     """Stationary <sigma> (3x3, per chain, kT units) of the Euler scheme for a
     Rouse chain (no slip-springs) under a constant velocity gradient: the bond
     vectors Q [N-1][3] obey Q' = Mq Q + dt Q kappa^T + D W sqrt(2 kT dt/zeta),
@@ -131,6 +131,13 @@ def sheared_rouse_stress(N, k_b, dt, zeta, kT, kappa):
     Mq = np.eye(n) - (dt * k_b / zeta) * DDt
     T = np.kron(np.eye(3), Mq) + dt * np.kron(kappa, np.eye(n))
     Sig = (2.0 * kT * dt / zeta) * np.kron(np.eye(3), DDt)
+    if scheme == "heun":
+        # stochastic Heun: q' = (I + h Dr + h^2 Dr^2/2) q + (I + h Dr/2) xi with
+        # the drift operator Dr = (T - I)/h
+        hD = T - np.eye(3 * n)
+        B = np.eye(3 * n) + 0.5 * hD
+        T = np.eye(3 * n) + hD + 0.5 * hD @ hD
+        Sig = B @ Sig @ B.T
     C = scipy.linalg.solve_discrete_lyapunov(T, Sig)
     sig = np.zeros((3, 3))
     for a in range(3):

@@ -43,7 +43,7 @@ MUTATIONS = [
     ("bead flow with the wrong sign", "mob * F[i][a] + p->dt * flow", "mob * F[i][a] - p->dt * flow",
      ["test_oracle_flow::test_frozen_beads_follow_linear_flow_map",
       "test_oracle_flow::test_sheared_rouse_steady_stress_matches_lyapunov"]),
-    ("anchor advection without dt", "An[a] = c->A[j][a] + p->dt * flow;", "An[a] = c->A[j][a] + flow;",
+    ("anchor advection without dt", "An[j][a] = c->A[j][a] + p->dt * flow;", "An[j][a] = c->A[j][a] + flow;",
      ["test_oracle_flow::test_frozen_anchors_follow_linear_flow_map",
       "test_oracle_flow::test_flow_schedule_switches_exactly_at_from_step"]),
     ("schedule switches a step early", "if (e->flow[i].from <= t) k = e->flow[i].k;",
@@ -56,6 +56,16 @@ MUTATIONS = [
      ["test_oracle_flow::test_spring_vector_variance_in_dynamics_with_frozen_beads"]),
     ("noise amplitude without the 2", "sqrt(2.0 * p->kT * p->dt / p->zeta)", "sqrt(p->kT * p->dt / p->zeta)",
      ["test_oracle_observables::test_rouse_closed_form_autocorrelation"]),
+    ("Heun corrector with the full mobility", "const double hmob = 0.5 * mob, hdt = 0.5 * p->dt;",
+     "const double hmob = mob, hdt = 0.5 * p->dt;",
+     ["test_oracle_heun::test_heun_rouse_closed_form_autocorrelation"]),
+    ("Heun corrector flow without the half", "const double hmob = 0.5 * mob, hdt = 0.5 * p->dt;",
+     "const double hmob = 0.5 * mob, hdt = p->dt;",
+     ["test_oracle_heun::test_heun_frozen_beads_and_anchors_follow_second_order_flow_map",
+      "test_oracle_heun::test_heun_sheared_rouse_matches_lyapunov"]),
+    ("Heun corrector forces at the start state", "if (i > 0) f += p->k_b * (Rn[i - 1][a] - Rn[i][a]);",
+     "if (i > 0) f += p->k_b * (c->R[i - 1][a] - c->R[i][a]);",
+     ["test_oracle_heun::test_heun_rouse_closed_form_autocorrelation"]),
     ("Glauber exponent doubled", "p->k_s * (d_new - d_old) / (4.0 * p->kT)",
      "p->k_s * (d_new - d_old) / (2.0 * p->kT)",
      ["test_oracle_model::test_hop_detailed_balance_frozen_beads",

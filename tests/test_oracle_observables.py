@@ -72,7 +72,10 @@ def test_multitau_tt_channel_equals_batch_definition(T):
 
 
 # -------------------------------------------------------------- Rouse -------
-def _rouse_exact(N, k_b, dt, zeta, kT, levels):
+def _rouse_exact(N, k_b, dt, zeta, kT, levels, scheme="euler"):
+    """Exact stress autocorrelation of the discrete scheme (see the module
+    docstring); scheme "heun": the stochastic Heun step maps each bond mode by
+    r = 1 - x + x^2/2 and scales its noise by (1 - x/2), x = k_b dt mu/zeta."""
     L = np.zeros((N, N))
     for i in range(N - 1):
         L[i, i] += 1
@@ -80,8 +83,13 @@ def _rouse_exact(N, k_b, dt, zeta, kT, levels):
         L[i, i + 1] -= 1
         L[i + 1, i] -= 1
     mu = np.linalg.eigvalsh(L)[1:]
-    r = 1 - k_b * dt * mu / zeta
-    V = (2 * kT * dt / zeta) / (1 - r ** 2)
+    x = k_b * dt * mu / zeta
+    if scheme == "heun":
+        r = 1 - x + x * x / 2
+        V = (2 * kT * dt / zeta) * (1 - x / 2) ** 2 / (1 - r ** 2)
+    else:
+        r = 1 - x
+        V = (2 * kT * dt / zeta) / (1 - r ** 2)
     amp = k_b ** 2 * mu ** 2 * V ** 2
 
     def C(n):
