@@ -12,12 +12,30 @@ stress, correlator).  `value` is whole-job bead-steps/s with the state resident
 in HBM; `e2e` is the same metric through the C ABI with the state copied in
 from host memory and G(t) read back every step; `plain` is the one-step-per-
 launch form of the same library (state through HBM every step, FP64 flush of
-the correlator every step).  --impl reference times the FP64 CPU oracle on a
-bounded sample of the same workload.
+the correlator every step).
+
+Further blocks of the JSON line (outside the timed region):
+  batched    the batched multiscale workload (4096 elements, ensemble sizes
+             log-uniform in 64..1024, lengths in {16, 24, 32, 48}, traceless
+             Gaussian velocity gradients redrawn every 1000 steps) in one
+             graph-replayed persistent launch per chunk: bead-steps/s from
+             CUDA events over --batched-steps steps, its ALU roofline and the
+             ratio to the plain per-ensemble form.
+  precision  error of the FP32 library against the FP64 oracle per output:
+             G(t) AUTO/CROSS/TOTAL at long lags and eta+(t), N1, <Z> at the 8
+             startup-shear rates against the stored oracle reference
+             (tests/golden/longrun_*_oracle.txt), and the short-lag G(t) of the
+             benchmark run against the cpu_baseline leg's oracle ensemble.
+The ALU roofline's numerator is the oracle's operation count per bead-step
+(tests/golden/alg_ops.txt, written by the counting build of the oracle); the
+peak is the device's SM count x 128 lanes x the SM clock sampled during the
+timed region.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload.
 """
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -28,31 +46,30 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
 
+import longrun_parity  # noqa: E402  (reads the stored oracle reference; runs only the library)
 import synth  # noqa: E402
 
-# ---- algorithmic work per bead-step (N = 32, <Z>/N = 1/N0 = 0.25, kappa = 0)
-# Counted per bead and step as scalar operations of the method, a multiply-add
-# and a three-input logic operation counting once, a transcendental once.
-ALG_OPS = {
-    "philox_block": 10 * 6,          # 10 rounds x (2 wide multiplies, 2 xor3, 2 key adds)
-    "box_muller_2pairs": 2 * 11,     # 2 x (2 cvt, 2 scale, log, x-2, sqrt, sin, cos, 2 mul)
-    "uniform24": 5,                  # byte extract/merge, cvt, scale
-    "bond_force": 3 * 4,             # 2 differences + 2 fma per component
-    "euler_update": 3 * 2,           # R + mob F + amp n
-    "spring_force": 0.25 * 3 * 2,    # per spring: difference + fma per component
-    "hop": 0.25 * 44,                # 3 squared distances, 2 Glauber probabilities, decision
-    "create_attempt": 0.75 * 2,      # empty slots: two comparisons
-    "destroy_test": 0.06 * 1,
-    "stress": 3 + 6 + 0.25 * 9 + 6,  # bond vector, 3 off-diagonal products, springs, sums
-    "correlator": (96 + 60) / 32.0,  # per chain: 2 ch x 16 lags x 3 comps + higher levels
-}
-ALG_OPS_PER_BEAD_STEP = float(sum(ALG_OPS.values()))
-SMS, LANES_PER_SM, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
-# DRAM bytes (read + write) of one chain-kernel launch of 1024 steps, per chain:
-# ncu capture of 16384 chains x 1024 steps (profiles/chunk_kernel_16x2_small_full.md),
-# 17.3 MB read + 363.5 MB written; every term scales with the chain count.
-TRAFFIC_BYTES_PER_CHAIN_1024 = 380.2e6 / 16384
+LANES_PER_SM = 128  # FP32/INT32 lanes of a Blackwell SM: 4 schedulers x 32, one instruction per clock each
+ALG_OPS_FILE = os.path.join(ROOT, "tests", "golden", "alg_ops.txt")
+# DRAM bytes (read + write) of one chain-kernel launch of 1024 steps, per chain, from the ncu
+# capture of 16384 chains x 1024 steps summarised in profiles/ (every term scales with the chain
+# count); None until the current kernel has been captured
+TRAFFIC_BYTES_PER_CHAIN_1024 = None
+
+
+def alg_ops():
+    """Operations of the method per bead-step by workload, from the stored counts of
+    the oracle's counting build: {name: {"total": x, category: x}}."""
+    out, cats = {}, None
+    for ln in open(ALG_OPS_FILE):
+        if ln.startswith("# name"):
+            cats = ln.split()[2:]
+        elif ln.strip() and not ln.startswith("#"):
+            f = ln.split()
+            out[f[0]] = dict(zip(cats, [float(x) for x in f[1:]]))
+    return out
 
 
 def _peaks():
@@ -61,6 +78,17 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 class ClockSampler:
@@ -137,6 +165,90 @@ def _barrier(ws):
         dist.barrier()
 
 
+def _peak(sms, clk):
+    """ALU issue peak in lane-ops/s at the SM clock clk (MHz) and its basis."""
+    mhz = clk.get("sm_max_mhz") or _peaks().get("sm_max_mhz") or 2070.0
+    return sms * LANES_PER_SM * mhz * 1e6, "%d SMs (device) x %d lanes x %.0f MHz (max SM clock sampled during " \
+        "the timed region), 1 lane-op per lane per clock" % (sms, LANES_PER_SM, mhz)
+
+
+def run_batched(args, stream, rank, sms, ops_by_n):
+    """The batched multiscale workload: one graph-replayed persistent launch per chunk."""
+    import torch
+
+    from paper_1106_2899_gb300 import SlipSpring
+    w = synth.WORKLOADS["batched"]
+    warm, steps, every = 1000, args.batched_steps, w["kappa_every"]
+    n_k = (warm + steps) // every + 1
+    Ms, Ns, G = synth.element_table(w["n_elements"], seed=w["seed"], lengths=w["lengths"], m_lo=w["m_lo"],
+                                    m_hi=w["m_hi"], n_kappa=n_k, kappa_std=w["kappa_std"])
+    els = [(int(m), int(n)) for m, n in zip(Ms, Ns)]
+    g = SlipSpring(els, precision="fp32", seed=w["seed"] + 1000 * rank, stream=stream.cuda_stream)
+    g.set_params(**synth.PAPER, corr_levels=-1, groups=4, log_every=100, max_logs=(warm + steps) // 100,
+                 chunk_steps=1000)
+    g.set_batched(True)
+    g.set_flow_table(np.repeat(np.arange(len(els)), n_k), np.tile(np.arange(n_k) * every, len(els)),
+                     G.reshape(-1, 3, 3))
+    g.run(0)
+    g.run(warm)  # autotune and the first graph launches
+    torch.cuda.synchronize()
+    c0 = g.counters()["launches"]
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    g.run(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b)
+    status = g.status()
+    launches = g.counters()["launches"] - c0
+    g.close()
+    beads = float(sum(m * n for m, n in els))
+    ops = sum(m * n * ops_by_n["flow_%d" % n]["total"] for m, n in els) / beads
+    value = beads * steps / (ms / 1e3)
+    peak, basis = _peak(sms, clk)
+    return {"value": value, "unit": "bead-steps/s", "steps": steps, "ms": ms,
+            "workload": "batched multiscale: %d elements, %d chains, %.4g beads (N in %s), FP32 beads / FP64 "
+                        "per-element stress sums, kappa redrawn every %d steps" % (
+                            len(els), int(sum(Ms)), beads, list(w["lengths"]), every),
+            "roofline": {"bound": "alu", "achieved": ops * value, "peak": peak, "unit": "lane-ops/s",
+                         "frac": ops * value / peak, "alg_ops_per_bead_step": ops,
+                         "kernel": "batched_kernel (all lane-layout classes of one graph launch per chunk, "
+                                   "timed together with CUDA events)", "peak_basis": basis, "traffic": None},
+            "clocks": clk, "status": status, "gpu_launches": int(launches)}
+
+
+def run_precision(stream):
+    """FP32 library against the stored FP64 oracle reference, per output."""
+    ref_G = longrun_parity.load_G()
+    res_G = longrun_parity.compare_G(longrun_parity.gpu_G(stream=stream.cuda_stream), ref_G)
+    steady, logs = longrun_parity.load_eta()
+    rates = synth.WORKLOADS["shear"]["rates"]
+    res_eta = longrun_parity.compare_eta(longrun_parity.gpu_eta(rates, stream=stream.cuda_stream), steady, logs,
+                                         rates)
+    out = {"criterion": "|delta| <= 3 sqrt(SE_gpu^2 + SE_oracle^2) at every lag/time, and <= 2% where the "
+                        "oracle's relative SE < 0.5%",
+           "G": {ch: {k: v for k, v in r.items() if k != "failures"} | {"failures": len(r["failures"])}
+                 for ch, r in res_G.items()},
+           "G_workload": "equilibrium N=32, 65536 GPU chains vs 2048 oracle chains, 320000 steps"}
+    eta = {}
+    for k, r in res_eta.items():
+        eta["%.3g" % r["gdot"]] = {
+            q: {"max_z": r[q]["max_z"], "max_rel_err_where_resolved": r[q]["max_rel_err_where_resolved"],
+                "times": r[q]["times_compared"], "failures": len(r[q]["failures"])} for q in ("eta", "N1", "Z")}
+        eta["%.3g" % r["gdot"]]["steady_eta"] = {k2: r["steady_eta"][k2] for k2 in ("gpu", "gpu_se", "oracle",
+                                                                                     "oracle_se", "z")}
+    out["startup_shear"] = eta
+    out["shear_workload"] = "N=32, 16384 GPU chains vs 1024 oracle chains per rate, 200000 steps"
+    out["all_pass"] = all(v["failures"] == 0 for v in out["G"].values()) and all(
+        r[q]["failures"] == [] for r in res_eta.values() for q in ("eta", "N1", "Z")) and all(
+        r["steady_eta"]["ok"] for r in res_eta.values())
+    out["max_lag_steps"] = max(v["max_lag_steps"] for v in out["G"].values())
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -149,6 +261,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     build.build()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    ops = alg_ops()
     w = synth.WORKLOADS["lve"]
     M, N = args.chains, w["N"]
     spc = args.steps_per_call
@@ -190,13 +305,14 @@ def run_ours(args):
     value = bead_steps * ws / (ms_total / 1e3)
     kernel_ms = chain_ms / max(chain_launches, 1)
     steps_per_launch = spc * args.steps / max(chain_launches, 1)
-    alg_ops_launch = ALG_OPS_PER_BEAD_STEP * M * N * steps_per_launch
-    achieved = alg_ops_launch / (kernel_ms / 1e3)
-    peak = SMS * LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6
+    ops_lve = ops["lve"]["total"]
+    achieved = ops_lve * M * N * steps_per_launch / (kernel_ms / 1e3)
+    peak, basis = _peak(sms, clk)
     status = g.status()
-    tg, Gg, sg = g.correlator("total")
-    dt_step = synth.PAPER["dt"]
-    gpu_G = {int(round(tt / dt_step)): (float(a), float(b)) for tt, a, b in zip(tg, Gg, sg)}
+    gpu_G = {}
+    for ch in longrun_parity.CHANNELS:
+        tg, Gg, sg = g.correlator(ch)
+        gpu_G[ch] = {int(round(tt / synth.PAPER["dt"])): (float(a), float(b)) for tt, a, b in zip(tg, Gg, sg)}
     g.close()
 
     # ---------------- plain one-step-per-launch form (same library, chunk = 1)
@@ -242,9 +358,14 @@ def run_ours(args):
     d2h = 32 * w["levels"] * 96 * 8 + 4
     ge.close()
 
+    batched = None if args.no_batched else run_batched(args, stream, rank, sms, ops)
+    precision = None if (args.no_precision or rank != 0) else run_precision(stream)
+
     if rank != 0:
         return None
     pk = _peaks()
+    traffic = TRAFFIC_BYTES_PER_CHAIN_1024 * M if (TRAFFIC_BYTES_PER_CHAIN_1024 and
+                                                   abs(steps_per_launch - 1024) < 1e-9) else None
     out = {
         "metric": "bead-steps/s",
         "value": value,
@@ -270,19 +391,29 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-ops/s",
-                     "frac": achieved / peak,
-                     "traffic": TRAFFIC_BYTES_PER_CHAIN_1024 * M if abs(steps_per_launch - 1024) < 1e-9 else None,
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": "chunk_kernel<float, 16, 2, 0, 0>", "kernel_ms": kernel_ms,
                      "kernel_share_of_region": chain_ms / ms_total if ws == 1 else None,
-                     "alg_ops_per_bead_step": ALG_OPS_PER_BEAD_STEP,
-                     "peak_basis": "152 SMs x 128 lanes x 2070 MHz (nominal max clock), 1 lane-op/lane/clock"},
+                     "alg_ops_per_bead_step": ops_lve,
+                     "alg_ops_source": "oracle counting build (tests/golden/alg_ops.txt)",
+                     "alg_ops_by_substep": {k: v for k, v in ops["lve"].items() if k != "total"},
+                     "peak_basis": basis, "sms": sms, "device": props.name},
         "clocks": clk,
         "status": status,
         "hbm_peak_measured_gbs": pk.get("hbm_gbs"),
     }
+    if batched is not None:
+        batched["over_plain"] = batched["value"] / plain_value
+        out["batched"] = batched
+    if precision is not None:
+        out["precision"] = precision
     if not args.no_cpu_baseline:
         cb = cpu_baseline(args.cpu_chains, args.cpu_steps)
-        out["g_err_vs_oracle"] = g_error(gpu_G, cb.pop("_G"))
+        ora = cb.pop("_G")
+        short = {ch: g_error(gpu_G[ch], ora[ch]) for ch in longrun_parity.CHANNELS}
+        if precision is not None:
+            precision["short_lag_vs_cpu_baseline"] = short
+        out["g_err_vs_oracle"] = short["total"]
         out["cpu_baseline"] = cb
     return out
 
@@ -299,19 +430,23 @@ def cpu_baseline(M=4096, steps=3000, nthreads=0):
     t = time.perf_counter()
     e.run(steps, nthreads=nthreads)
     dt = time.perf_counter() - t
-    # G(t) of the TOTAL channel per multiple-tau slot, mean and SE over the 32 groups
+    # G(t) per channel and multiple-tau slot, mean and SE over the 32 groups
     acc, n = e.corr_sums()
     cnt = oracle.corr_counts(n, w["levels"])
     lags = oracle.corr_lags(w["levels"])
     per_group = np.array([(g + 1) * M // 32 - g * M // 32 for g in range(32)], dtype=float)
-    G = {}
+    G = {ch: {} for ch in longrun_parity.CHANNELS}
     for l in range(w["levels"]):
         for k in range(16):
             if lags[l, k] < 0 or cnt[l, k] <= 0:
                 continue
-            gk = acc[:, l, k, 1, :].sum(axis=-1) / 3.0 / (cnt[l, k] * per_group * w["N"] * p.kT * p.kT)
-            G[int(lags[l, k])] = (float(gk.mean()), float(gk.std(ddof=1) / np.sqrt(len(gk))))
+            norm = cnt[l, k] * per_group * w["N"] * p.kT * p.kT
+            auto = acc[:, l, k, 0, :].sum(axis=-1) / 3.0 / norm
+            total = acc[:, l, k, 1, :].sum(axis=-1) / 3.0 / norm
+            for ch, v in zip(longrun_parity.CHANNELS, (auto, total - auto, total)):
+                G[ch][int(lags[l, k])] = (float(v.mean()), float(v.std(ddof=1) / np.sqrt(len(v))))
     return {"value": M * w["N"] * steps / dt, "unit": "bead-steps/s", "cores": nthreads, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": "%d chains x N=%d x %d steps of the lve workload (correlator 16x24), %.1f s" % (
                 M, w["N"], steps, dt), "_G": G}
 
@@ -331,7 +466,7 @@ def g_error(gpu, ora, max_lag=2000):
     if not zs:
         return None
     zs = np.array(zs)
-    return {"channel": "TOTAL", "lags_compared": int(len(zs)), "max_lag_steps": max_lag,
+    return {"lags_compared": int(len(zs)), "max_lag_steps": max_lag,
             "max_z": float(zs.max()), "frac_z_below_3": float(np.mean(zs < 3.0)),
             "max_rel_err_where_resolved": float(max(rel)) if rel else None, "resolved_lags": len(rel),
             "oracle": "independent FP64 ensemble of the cpu_baseline leg (other chains)"}
@@ -354,7 +489,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "lve: 65536 chains x N=32 (bounded sample: %d chains per step)" % args.cpu_chains},
             "cpu_baseline": {"value": value, "unit": "bead-steps/s", "cores": cb["cores"], "kind": "oracle",
-                             "sample": cb["sample"]},
+                             "cpu": cb["cpu"], "sample": cb["sample"]},
             "e2e": {"value": value, "unit": "bead-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -368,9 +503,12 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=2048)
     ap.add_argument("--chunk", type=int, default=1024)
     ap.add_argument("--plain-steps", type=int, default=200)
+    ap.add_argument("--batched-steps", type=int, default=10000)
     ap.add_argument("--cpu-chains", type=int, default=4096)
     ap.add_argument("--cpu-steps", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -112,7 +112,22 @@ typedef struct {
                                so its sums depend on it at the rounding level        */
     int32_t corr_tt;        /* 1: also correlate sigma + sigma^(v) with itself (channels
                                SS_CH_TT, SS_CH_VIRTUAL) [0]                             */
+    int32_t integrator;     /* substep 1: SS_EULER, the Euler-Maruyama scheme of Sec. 3.1
+                               [default], or SS_HEUN, the stochastic Heun scheme (the
+                               second-order stochastic Runge-Kutta method for additive
+                               noise that Sec. 3.1 names as the more accurate choice):
+                               the Euler step predicts, the corrector averages the drift
+                               (bead forces with this step's springs, flow terms) at the
+                               start and at the predicted beads and anchors, with the
+                               same noise; hops, creation and destruction unchanged.
+                               Stationary bias O(dt^2) instead of O(dt).  The per-element
+                               path only: batched mode, differentiation windows and
+                               ss_run_noalloc refuse it with SS_EINVAL               */
 } ss_params;
+
+/* integrators (ss_params.integrator) */
+#define SS_EULER 0
+#define SS_HEUN 1
 
 /* Create a context for n_elems elements.  precision: SS_FP32 or SS_FP64.
  * seed keys the counter-based random numbers (Philox4x32-10): chains with the

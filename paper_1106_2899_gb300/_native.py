@@ -13,6 +13,7 @@ ERRORS = {-1: "SS_EINVAL", -2: "SS_ENOMEM", -3: "SS_ECUDA", -4: "SS_EOVERFLOW", 
           -6: "SS_ETIMEOUT", -7: "SS_ETOOBIG"}
 SS_NOALLOC_SCRATCH_BYTES = 32 << 20
 SS_FP32, SS_FP64 = 0, 1
+SS_EULER, SS_HEUN = 0, 1
 SS_MAX_BEADS, SS_MAX_SLOTS = 128, 64
 SS_CH_AUTO, SS_CH_CROSS, SS_CH_TOTAL, SS_CH_TT, SS_CH_VIRTUAL = 0, 1, 2, 3, 4
 
@@ -36,7 +37,7 @@ class ss_params(C.Structure):
                 ("k_s", C.c_double), ("create_mode", C.c_int32), ("z_max", C.c_int32),
                 ("destroy_new", C.c_int32), ("recenter_every", C.c_int32), ("log_every", C.c_int32),
                 ("max_logs", C.c_int32), ("corr_levels", C.c_int32), ("groups", C.c_int32),
-                ("chunk_steps", C.c_int32), ("corr_tt", C.c_int32)]
+                ("chunk_steps", C.c_int32), ("corr_tt", C.c_int32), ("integrator", C.c_int32)]
 
 
 class SlipSpringError(RuntimeError):

@@ -240,6 +240,8 @@ ssk::StepConst<T> step_const(const ss_ctx* c, int N) {
     }
     s.two_pref = T(2.0 * p.dt * p.kT / p.zeta_s);
     s.c2 = T(2.0 * (c->k_s / (4.0 * p.kT)) * 1.4426950408889634);
+    s.hmob = T(0.5 * (p.dt / p.zeta));
+    s.hdt = T(0.5 * p.dt);
     uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
     for (int r = 0; r < 10; ++r) {
         s.rk0[r] = k0;
@@ -355,7 +357,9 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     const bool win = c->opt_tape_mode != 0 || c->opt_snap;
     void (*kern)(const ssk::ChunkArgs, const ssk::StepConst<T>) =
         win ? ssk::chunk_kernel<T, W, B, true, true> : ssk::chunk_kernel<T, W, B, false, true>;
-    if constexpr (std::is_same<T, float>::value) {
+    if (c->P.integrator == SS_HEUN) {
+        kern = ssk::chunk_kernel<T, W, B, false, true, true>;  // windows refuse this integrator
+    } else if constexpr (std::is_same<T, float>::value) {
         if (!win && !flow_in_window(e, t0, nsteps)) kern = ssk::chunk_kernel<T, W, B, false, false>;
     }
     // the attribute belongs to the current device: set it on every launch that
@@ -1183,6 +1187,8 @@ int ss_set_params(ss_ctx* c, const ss_params* pin) {
         return fail(c, SS_EINVAL, "Euler step unstable: dt (4 k_b + k_s) / zeta must be < 2");
     if (p.create_mode != 0 && p.create_mode != 1) return fail(c, SS_EINVAL, "create_mode must be 0 or 1");
     if (p.corr_tt != 0 && p.corr_tt != 1) return fail(c, SS_EINVAL, "corr_tt must be 0 or 1");
+    if (p.integrator != SS_EULER && p.integrator != SS_HEUN)
+        return fail(c, SS_EINVAL, "integrator must be SS_EULER or SS_HEUN");
     if (p.destroy_new != 0 && p.destroy_new != 1) return fail(c, SS_EINVAL, "destroy_new must be 0 or 1");
     if (p.corr_levels > SS_MAX_LEVELS) return fail(c, SS_EINVAL, "corr_levels must be <= 32");
     if (p.groups < 1 || p.chunk_steps < 1 || p.log_every < 0 || p.max_logs < 0)
@@ -1303,6 +1309,7 @@ int ss_run(ss_ctx* c, int64_t n_steps) {
     }
     if (c->batched) {
         if (c->levels > 0) return fail(c, SS_EINVAL, "batched mode keeps stress logs only: set corr_levels < 0");
+        if (p.integrator != SS_EULER) return fail(c, SS_EINVAL, "batched mode runs the Euler-Maruyama integrator");
         return c->prec == SS_FP64 ? batched_run<double>(c, n_steps) : batched_run<float>(c, n_steps);
     }
     long long left = n_steps;
@@ -1673,6 +1680,8 @@ int ss_window_forward(ss_ctx* c, int64_t n_steps, int checkpoint_every, int repl
     if (c->el.size() != 1) return fail(c, SS_EINVAL, "a differentiation window needs exactly one element");
     if (c->levels <= 0) return fail(c, SS_EINVAL, "a differentiation window needs the correlator (corr_levels > 0)");
     if (c->batched) return fail(c, SS_EINVAL, "a differentiation window runs on the per-element path");
+    if (c->P.integrator != SS_EULER)
+        return fail(c, SS_EINVAL, "differentiation windows differentiate the Euler-Maruyama step");
     if (checkpoint_every < 1 || n_steps < 1) return fail(c, SS_EINVAL, "n_steps, checkpoint_every must be >= 1");
     if (checkpoint_every > c->P.chunk_steps) return fail(c, SS_EINVAL, "checkpoint_every must be <= chunk_steps");
     Elem& e = c->el[0];
@@ -1885,7 +1894,7 @@ extern "C" int ss_run_noalloc(const ss_params* params, int precision, uint64_t s
     if (n_chains <= 0 || n_beads < 2 || n_beads > SS_MAX_BEADS || t0 < 0 || n_steps < 0) return SS_EINVAL;
     if ((long long)chain_base + n_chains > 0xFFFFFFFFll) return SS_EINVAL;
     if (t0 + n_steps > 0xFFFFFFFFll) return SS_EOVERFLOW;
-    if (params->log_every != 0) return SS_EINVAL;
+    if (params->log_every != 0 || params->integrator != SS_EULER) return SS_EINVAL;
     if (kappa)
         for (int i = 0; i < 9; ++i)
             if (!std::isfinite(kappa[i])) return SS_EINVAL;

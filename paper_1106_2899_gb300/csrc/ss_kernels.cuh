@@ -218,6 +218,7 @@ struct StepConst {
     T pc[kMaxSlots + 1];  // creation probability per end and attempt, by K
     T two_pref;           // 2 dt kT / zeta_s
     T c2;                 // 2 chop log2(e): base-2 exponent per change of squared length
+    T hmob, hdt;          // mob / 2, dt / 2: the stochastic Heun corrector
     uint32_t rk0[10], rk1[10];  // Philox round keys (key + r * Weyl increment)
 };
 
@@ -432,7 +433,7 @@ __device__ __forceinline__ void snapshot_store(const ChunkArgs& a, long long row
 // the element described by `a` (all warps of the CTA call this together).
 // FLOW: the velocity-gradient terms are compiled in (without them the launch
 // must have kappa = 0 throughout; recentring is then never needed).
-template <typename T, int W, int B, bool WIN, bool FLOW>
+template <typename T, int W, int B, bool WIN, bool FLOW, bool HEUN = false>
 __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T>& c, const int cta_first,
                                            const T NkT, const long long t0_, const int nsteps_,
                                            const long long log_m0_, const int nlog_) {
@@ -619,56 +620,73 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             if (i < Z) atomicOr(&msk[S[b]], Mask(1) << i);
         }
 
-        // ---- substep 1: forces at time t, Euler-Maruyama, anchor advection
-        T F[B][3];
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const int i = ll + b * W;
-            const Pos<T> pl = pos[i > 0 ? i - 1 : 0];
-            const Pos<T> pr = pos[i < N - 1 ? i + 1 : i];
-            const T Rl[3] = {pl.x, pl.y, pl.z}, Rr[3] = {pr.x, pr.y, pr.z};
-            // an end bead reads itself for its missing neighbour: that term is 0
-#pragma unroll
-            for (int d = 0; d < 3; ++d) F[b][d] = c.k_b * (Rl[d] - R[b][d]) + c.k_b * (Rr[d] - R[b][d]);
-        }
-        __syncwarp();
-        bool more = false;
-        Mask mrest[B];
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            // springs on this bead: -k_s sum_j d_j, slots in ascending order
-            // (an empty mask reads the zero record at NP)
-            const Mask m0 = msk[ll + b * W];
-            const Mask m1 = m0 & (m0 - Mask(1));
-            const int j0 = m0 ? mask_ffs(m0) - 1 : NP;
-            const int j1 = m1 ? mask_ffs(m1) - 1 : NP;
-            const SlotRec<T> r0 = tab[j0], r1 = tab[j1];
-            const Mask mb = m1 & (m1 - Mask(1));
-            mrest[b] = mb;
-            more |= mb != Mask(0);
-            F[b][0] -= c.k_s * (r0.x + r1.x);
-            F[b][1] -= c.k_s * (r0.y + r1.y);
-            F[b][2] -= c.k_s * (r0.z + r1.z);
-        }
-        if (__any_sync(kFull, more)) {  // a third spring on one bead: rare
+        // ---- substep 1: forces at time t, Euler-Maruyama, anchor advection.
+        // Forces on positions Ro (this lane's beads; the other beads from the
+        // position table) with the spring vectors of the slot table: bonds
+        // k_b (R_{i-1} + R_{i+1} - 2 R_i), springs -k_s sum_{j: S_j = i} d_j.
+        auto forces = [&](T (&Fo)[B][3], const T (&Ro)[B][3]) {
 #pragma unroll
             for (int b = 0; b < B; ++b) {
-                // the first two slots were added already; add the rest in order
-                Mask mb = mrest[b];
-                T sx = T(0), sy = T(0), sz = T(0);
-                while (mb) {
-                    const SlotRec<T> r = tab[mask_ffs(mb) - 1];
-                    mb &= mb - Mask(1);
-                    sx += r.x;
-                    sy += r.y;
-                    sz += r.z;
-                }
-                F[b][0] -= c.k_s * sx;
-                F[b][1] -= c.k_s * sy;
-                F[b][2] -= c.k_s * sz;
+                const int i = ll + b * W;
+                const Pos<T> pl = pos[i > 0 ? i - 1 : 0];
+                const Pos<T> pr = pos[i < N - 1 ? i + 1 : i];
+                const T Rl[3] = {pl.x, pl.y, pl.z}, Rr[3] = {pr.x, pr.y, pr.z};
+                // an end bead reads itself for its missing neighbour: that term is 0
+#pragma unroll
+                for (int d = 0; d < 3; ++d) Fo[b][d] = c.k_b * (Rl[d] - Ro[b][d]) + c.k_b * (Rr[d] - Ro[b][d]);
             }
-        }
+            __syncwarp();
+            bool more = false;
+            Mask mrest[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                // springs on this bead: -k_s sum_j d_j, slots in ascending order
+                // (an empty mask reads the zero record at NP)
+                const Mask m0 = msk[ll + b * W];
+                const Mask m1 = m0 & (m0 - Mask(1));
+                const int j0 = m0 ? mask_ffs(m0) - 1 : NP;
+                const int j1 = m1 ? mask_ffs(m1) - 1 : NP;
+                const SlotRec<T> r0 = tab[j0], r1 = tab[j1];
+                const Mask mb = m1 & (m1 - Mask(1));
+                mrest[b] = mb;
+                more |= mb != Mask(0);
+                Fo[b][0] -= c.k_s * (r0.x + r1.x);
+                Fo[b][1] -= c.k_s * (r0.y + r1.y);
+                Fo[b][2] -= c.k_s * (r0.z + r1.z);
+            }
+            if (__any_sync(kFull, more)) {  // a third spring on one bead: rare
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    // the first two slots were added already; add the rest in order
+                    Mask mb = mrest[b];
+                    T sx = T(0), sy = T(0), sz = T(0);
+                    while (mb) {
+                        const SlotRec<T> r = tab[mask_ffs(mb) - 1];
+                        mb &= mb - Mask(1);
+                        sx += r.x;
+                        sy += r.y;
+                        sz += r.z;
+                    }
+                    Fo[b][0] -= c.k_s * sx;
+                    Fo[b][1] -= c.k_s * sy;
+                    Fo[b][2] -= c.k_s * sz;
+                }
+            }
+        };
+        T F[B][3];
+        forces(F, R);
+        // Padding beads (i >= N) are stepped like the others: they hang from
+        // bead N-1 by a one-sided bond, exert no force, carry no spring and
+        // enter no stress (their bond vector reads themselves), and they are
+        // never stored.
         T Rn[B][3];
+        [[maybe_unused]] T A0[B][3];
+        if constexpr (HEUN) {
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) A0[b][d] = A[b][d];
+        }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
@@ -687,8 +705,8 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                                 pk(c.amp), pk(nrm[b][d], nrm[b + 1][d]),
                                 __ffma2_rn(pk(c.dt), flow,
                                            __ffma2_rn(pk(c.mob), pk(F[b][d], F[b + 1][d]), pk(R[b][d], R[b + 1][d]))));
-                            Rn[b][d] = (i < N) ? e.x : T(0);
-                            Rn[b + 1][d] = (i + W < N) ? e.y : T(0);
+                            Rn[b][d] = e.x;
+                            Rn[b + 1][d] = e.y;
                         }
                     }
                 } else if constexpr (std::is_same<T, float>::value) {
@@ -696,15 +714,13 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                     for (int d = 0; d < 3; ++d) {
                         const float flow = __fmaf_rn(kap[3 * d + 2], R[b][2],
                                                      __fmaf_rn(kap[3 * d + 1], R[b][1], __fmul_rn(kap[3 * d], R[b][0])));
-                        Rn[b][d] = (i < N) ? __fmaf_rn(c.amp, nrm[b][d],
-                                                       __fmaf_rn(c.dt, flow, __fmaf_rn(c.mob, F[b][d], R[b][d])))
-                                           : T(0);
+                        Rn[b][d] = __fmaf_rn(c.amp, nrm[b][d], __fmaf_rn(c.dt, flow, __fmaf_rn(c.mob, F[b][d], R[b][d])));
                     }
                 } else {
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         const T flow = kap[3 * d] * R[b][0] + kap[3 * d + 1] * R[b][1] + kap[3 * d + 2] * R[b][2];
-                        Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d]) : T(0);
+                        Rn[b][d] = R[b][d] + c.mob * F[b][d] + c.dt * flow + c.amp * nrm[b][d];
                     }
                 }
             } else if constexpr (PK) {
@@ -714,14 +730,13 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                         const float2 e = __ffma2_rn(pk(c.amp), pk(nrm[b][d], nrm[b + 1][d]),
                                                     __ffma2_rn(pk(c.mob), pk(F[b][d], F[b + 1][d]),
                                                                pk(R[b][d], R[b + 1][d])));
-                        Rn[b][d] = (i < N) ? e.x : T(0);
-                        Rn[b + 1][d] = (i + W < N) ? e.y : T(0);
+                        Rn[b][d] = e.x;
+                        Rn[b + 1][d] = e.y;
                     }
                 }
             } else {
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    Rn[b][d] = (i < N) ? (R[b][d] + c.mob * F[b][d] + c.amp * nrm[b][d]) : T(0);
+                for (int d = 0; d < 3; ++d) Rn[b][d] = R[b][d] + c.mob * F[b][d] + c.amp * nrm[b][d];
             }
             if (kap_nz && i < Z) {
                 T An[3];
@@ -730,6 +745,65 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                     An[d] = A[b][d] + c.dt * (kap[3 * d] * A[b][0] + kap[3 * d + 1] * A[b][1] + kap[3 * d + 2] * A[b][2]);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) A[b][d] = An[d];
+            }
+        }
+        if constexpr (HEUN) {
+            // Stochastic Heun corrector (the second-order stochastic Runge-Kutta
+            // step for additive noise): the Euler state above is the predictor;
+            // the drift is averaged between the start and the predicted state
+            // (predicted anchors A under a flow), with the springs and the
+            // noise of this step.
+            __syncwarp();
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                Pos<T> pn;
+                pn.x = Rn[b][0];
+                pn.y = Rn[b][1];
+                pn.z = Rn[b][2];
+                pn.w = T(0);
+                pos[ll + b * W] = pn;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int i = ll + b * W;
+                if (i < Z) {
+                    const Pos<T> ps = pos[S[b]];
+                    SlotRec<T> rec;
+                    rec.x = ps.x - A[b][0];
+                    rec.y = ps.y - A[b][1];
+                    rec.z = ps.z - A[b][2];
+                    rec.s = S[b];
+                    tab[i] = rec;
+                }
+            }
+            __syncwarp();
+            T F2[B][3];
+            forces(F2, Rn);
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int i = ll + b * W;
+                T fl[3] = {T(0), T(0), T(0)};
+                if (kap_nz) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        fl[d] = (kap[3 * d] * R[b][0] + kap[3 * d + 1] * R[b][1] + kap[3 * d + 2] * R[b][2]) +
+                                (kap[3 * d] * Rn[b][0] + kap[3 * d + 1] * Rn[b][1] + kap[3 * d + 2] * Rn[b][2]);
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    Rn[b][d] = R[b][d] + c.hmob * (F[b][d] + F2[b][d]) + c.hdt * fl[d] + c.amp * nrm[b][d];
+                if (kap_nz && i < Z) {
+                    T An[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        An[d] = A0[b][d] + c.hdt * ((kap[3 * d] * A0[b][0] + kap[3 * d + 1] * A0[b][1] +
+                                                     kap[3 * d + 2] * A0[b][2]) +
+                                                    (kap[3 * d] * A[b][0] + kap[3 * d + 1] * A[b][1] +
+                                                     kap[3 * d + 2] * A[b][2]));
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) A[b][d] = An[d];
+                }
             }
         }
         __syncwarp();
@@ -1134,12 +1208,13 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 // WIN: the differentiation-window hooks (decision tape, snapshots, stress
 // series) are compiled in; the plain kernel carries none of them.  FLOW: the
 // velocity-gradient terms are compiled in (launches with kappa = 0 throughout
-// may use the instantiation without them).
-template <typename T, int W, int B, bool WIN, bool FLOW>
+// may use the instantiation without them).  HEUN: the stochastic Heun
+// integrator instead of Euler-Maruyama for substep 1.
+template <typename T, int W, int B, bool WIN, bool FLOW, bool HEUN = false>
 __global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : (B >= 4 ? 4 : SS_CTAS_PER_SM_MULTI))
     chunk_kernel(const ChunkArgs a, const StepConst<T> c) {
-    run_chains<T, W, B, WIN, FLOW>(a, c, blockIdx.x * (kChunkThreads / W), c.NkT, a.t0, a.nsteps, a.log_m0,
-                                   a.nlog_chunk);
+    run_chains<T, W, B, WIN, FLOW, HEUN>(a, c, blockIdx.x * (kChunkThreads / W), c.NkT, a.t0, a.nsteps, a.log_m0,
+                                         a.nlog_chunk);
 }
 
 // ------------------------------------------------------ batched kernel ------

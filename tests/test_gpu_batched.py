@@ -20,6 +20,7 @@ import oracle
 import synth
 from oracle import Params
 from paper_1106_2899_gb300 import SlipSpring
+from test_gpu_parity import _compare_states
 
 pytestmark = pytest.mark.gpu
 
@@ -109,56 +110,77 @@ def test_batched_fp64_matches_oracle_on_sampled_chains():
 
 @pytest.mark.slow
 def test_multiscale_workload_full_size():
+    """The full workload for 1e4 steps.  48 sampled chains (one per sampled
+    element) are followed by the oracle with the same flow history: at every
+    100-step checkpoint before a chain's first near-tie (a decision whose
+    oracle margin is below 1e-5, where FP32 rounding may decide the other way)
+    the integers must be equal and positions within 1e-4 relative in the
+    chain's centre-of-mass frame; most sampled chains must reach a checkpoint.
+    Every chain's invariants are checked at the end."""
     w = synth.WORKLOADS["batched"]
+    steps, every, log_every, check_until, ck = 10000, w["kappa_every"], 100, 2000, 100
+    n_k = steps // every + 1
     Ms, Ns, G = synth.element_table(w["n_elements"], seed=w["seed"], lengths=w["lengths"], m_lo=w["m_lo"],
-                                    m_hi=w["m_hi"], n_kappa=3, kappa_std=w["kappa_std"])
+                                    m_hi=w["m_hi"], n_kappa=n_k, kappa_std=w["kappa_std"])
     els = [(int(m), int(n)) for m, n in zip(Ms, Ns)]
-    steps, every, log_every = 2000, w["kappa_every"], 100
     g = SlipSpring(els, precision="fp32", seed=w["seed"])
     g.set_params(**synth.PAPER, corr_levels=-1, groups=4, log_every=log_every, max_logs=steps // log_every,
                  chunk_steps=1000)
     g.set_batched(True)
-    elem = np.repeat(np.arange(len(els)), 2)
-    frm = np.tile([0, every], len(els))
-    kap = G[:, :2].reshape(-1, 3, 3)
-    g.set_flow_table(elem, frm, kap)
+    g.set_flow_table(np.repeat(np.arange(len(els)), n_k), np.tile(np.arange(n_k) * every, len(els)),
+                     G.reshape(-1, 3, 3))
     g.run(0)
     c0 = g.counters()
-    z0 = sum(int(g.get_state(e)["Z"].sum()) for e in range(0, len(els), 1))
-    g.run(1000)  # autotune + first graph launch
+    z0 = sum(int(g.get_state(e)["Z"].sum()) for e in range(len(els)))
+    base = np.concatenate([[0], np.cumsum(Ms)[:-1]])
+    rng = np.random.default_rng(0)
+    sample = sorted(rng.choice(len(els), size=48, replace=False).tolist())
+    picks = {e: int(rng.integers(els[e][0])) for e in sample}
+    gpu_ck = {e: [] for e in sample}
+    for t in range(ck, check_until + 1, ck):
+        g.run(ck)
+        for e in sample:
+            st = g.get_state(e)
+            m = picks[e]
+            gpu_ck[e].append({k: v[m:m + 1] for k, v in st.items()})
+    compared, chains_compared = 0, 0
+    for e in sample:
+        M, N = els[e]
+        o = oracle.Ensemble(Params(N=N, **synth.PAPER), seed=w["seed"], M=1, chain_offset=int(base[e] + picks[e]),
+                            levels=1)
+        for d in range(n_k):
+            o.set_flow(d * every, G[e, d])
+        o.init()
+        first_tie, nc = None, 0
+        for i in range(check_until // ck):
+            _, _, mg = o.run(ck, trace=True)
+            ties = np.nonzero(mg[:, 0] < 1e-5)[0]
+            if first_tie is None and len(ties):
+                first_tie = i * ck + int(ties[0])
+            if first_tie is not None:
+                break
+            _compare_states(gpu_ck[e][i], o.get_state(), np.ones(1, bool), 1e-4, "element %d step %d" % (e, (i + 1) * ck))
+            nc += 1
+        compared += nc
+        chains_compared += nc > 0
+    assert chains_compared >= 0.7 * len(sample), (chains_compared, len(sample))
+    assert compared >= 3 * len(sample)
     g.synchronize()
     t = time.perf_counter()
-    g.run(steps - 1000)
+    g.run(steps - check_until)
     g.synchronize()
     dt = time.perf_counter() - t
     beads = float(sum(m * n for m, n in els))
-    print("\nmultiscale workload: %d elements, %d chains, %.3g beads: %.3g bead-steps/s"
-          % (len(els), sum(m for m, _ in els), beads, beads * (steps - 1000) / dt))
+    print("\nmultiscale workload: %d elements, %d chains, %.3g beads: %.3g bead-steps/s (wall clock)"
+          % (len(els), sum(m for m, _ in els), beads, beads * (steps - check_until) / dt))
     assert g.status() == 0
     c = g.counters()
     zs = 0
-    base = 0
-    rng = np.random.default_rng(0)
-    sample = set(rng.choice(len(els), size=12, replace=False).tolist())
-    agree = 0
     for e, (M, N) in enumerate(els):
         st = g.get_state(e)
         assert np.all((st["Z"] >= 0) & (st["Z"] <= N)) and np.all(np.isfinite(st["R"]))
+        assert np.all((st["S"] < N) & ((st["S"] >= 0) == (np.arange(st["S"].shape[1])[None, :] < st["Z"][:, None])))
         zs += int(st["Z"].sum())
-        if e in sample:
-            m = int(rng.integers(M))
-            p = Params(N=N, **synth.PAPER)
-            o = oracle.Ensemble(p, seed=w["seed"], M=1, chain_offset=base + m, levels=1)
-            o.set_flow(0, kap[2 * e])
-            o.set_flow(every, kap[2 * e + 1])
-            o.init()
-            _, _, mg = o.run(steps, trace=True)
-            if not np.any(mg[:, 0] < 1e-5):
-                oo = o.get_state()
-                assert oo["Z"][0] == st["Z"][m] and np.array_equal(oo["S"][0], st["S"][m]), (e, m)
-                agree += 1
-        base += M
     assert zs - z0 == (c["created"] - c0["created"]) - (c["destroyed"] - c0["destroyed"])
-    assert agree >= 1
     t_log, L = g.log_sums(0)
     assert len(t_log) == steps // log_every

@@ -206,3 +206,55 @@ def test_flow_start_inside_a_launch_is_bit_identical(N):
             assert np.array_equal(a[k], b[k]), k
         for k in ("hops_up", "hops_down", "created", "destroyed"):
             assert ca[k] == cb[k], k
+
+
+@pytest.mark.slow
+def test_viscosity_growth_N40_thinning_overshoot_and_cox_merz():
+    """The viscosity-growth sweep of Sec. 4.1 (E4): N = 40 at the paper's rates
+    gdot tau0 = 0.0025 .. 0.1 (4096 chains per rate; the paper used 1024),
+    4e5 steps (strain 10 at the lowest rate, about 11 tau_d).  The paper finds
+    shear thinning with a steady shear stress that still increases with the
+    rate (no mechanical instability), a stress overshoot at the high rates,
+    and the Cox-Merz rule eta(gdot) ~ |eta*(w = gdot)| (Eqs. cox_merz_rule,
+    dynamic_viscosity_definition with the 1/w restored) at small rates, broken
+    at high rates where eta(gdot) levels off (the second-Newtonian regime)
+    while |eta*| keeps falling.  |eta*| comes from G(t) of the N = 40
+    equilibrium run of test_gpu_lve."""
+    from paper_1106_2899_gb300 import rheology
+    from test_gpu_lve import equilibrium_G
+
+    N, M, steps, log_every = 40, 4096, 400000, 100
+    rates = [0.0025, 0.005, 0.01, 0.025, 0.05, 0.1]
+    g = SlipSpring([(M, N)] * len(rates), precision="fp32", seed=40)
+    g.set_params(**synth.PAPER, corr_levels=-1, groups=32, log_every=log_every, max_logs=steps // log_every)
+    for e, gd in enumerate(rates):
+        g.set_flow(synth.shear_kappa(gd), 0, elem=e)
+    g.run(steps)
+    assert g.status() == 0
+    steady, se, peak = [], [], []
+    for e, gd in enumerate(rates):
+        t, mean, sem = g.stress(e)
+        eta = rheology.eta_plus(mean[:, 3], N, gd)
+        s, ss = rheology.steady_viscosity(eta, tail=0.5)
+        steady.append(s)
+        se.append(ss)
+        # overshoot: the largest 2-tau0 window mean of eta+ before the steady half
+        w = np.convolve(eta, np.ones(2), "valid") / 2
+        peak.append(w[: len(w) // 2].max())
+    steady, se, peak = np.array(steady), np.array(se), np.array(peak)
+    tg, G, _ = equilibrium_G(40)
+    ok = G > 0
+    Gp, Gpp = rheology.storage_loss_moduli(tg[ok], G[ok], rates)
+    star = rheology.dynamic_viscosity(Gp, Gpp, rates)
+    for gd, s, ss, pk, es in zip(rates, steady, se, peak, star):
+        print("gdot %.4g: eta %.3f +- %.3f, peak eta+ %.3f, |eta*| %.3f, ratio %.2f" % (gd, s, ss, pk, es, s / es))
+    # shear thinning, with a monotone steady stress
+    assert np.all(np.diff(steady) < 2 * (se[1:] + se[:-1])) and steady[-1] < 0.5 * steady[0]
+    assert np.all(np.diff(steady * np.array(rates)) > 0)
+    # stress overshoot at the two highest rates
+    for k in (4, 5):
+        assert peak[k] > 1.05 * steady[k] and peak[k] > steady[k] + 5 * se[k], (rates[k], peak[k], steady[k])
+    # Cox-Merz at the two lowest rates; broken at the highest
+    for k in (0, 1):
+        assert abs(steady[k] / star[k] - 1) < 0.25, (rates[k], steady[k], star[k])
+    assert steady[-1] / star[-1] > 1.2

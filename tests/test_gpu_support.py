@@ -32,9 +32,10 @@ def _poisson_chi2(hist, lam, zm):
     pm[zm] += stats.poisson.sf(zm, lam)  # the z_max cap collects the tail
     exp = pm * hist.sum()
     big = exp >= 5
-    obs = np.append(hist[big], hist[~big].sum())
-    ex = np.append(exp[big], exp[~big].sum())
-    return stats.chisquare(obs, ex)
+    obs, ex = hist[big], exp[big]
+    if (~big).any():  # lump the sparse bins into one
+        obs, ex = np.append(obs, hist[~big].sum()), np.append(ex, exp[~big].sum())
+    return stats.chisquare(obs, ex * obs.sum() / ex.sum())
 
 
 def test_zhist_parity_workload_matches_oracle_and_poisson(cuda_ok):
