@@ -180,7 +180,7 @@ def run_batched(args, stream, rank, sms, ops_by_n):
     w = synth.WORKLOADS["batched"]
     warm, steps, every = 1000, args.batched_steps, w["kappa_every"]
     n_k = (warm + steps) // every + 1
-    Ms, Ns, G = synth.element_table(w["n_elements"], seed=w["seed"], lengths=w["lengths"], m_lo=w["m_lo"],
+    Ms, Ns, G = synth.element_table(args.batched_elements, seed=w["seed"], lengths=w["lengths"], m_lo=w["m_lo"],
                                     m_hi=w["m_hi"], n_kappa=n_k, kappa_std=w["kappa_std"])
     els = [(int(m), int(n)) for m, n in zip(Ms, Ns)]
     g = SlipSpring(els, precision="fp32", seed=w["seed"] + 1000 * rank, stream=stream.cuda_stream)
@@ -511,6 +511,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=1024)
     ap.add_argument("--plain-steps", type=int, default=200)
     ap.add_argument("--batched-steps", type=int, default=10000)
+    ap.add_argument("--batched-elements", type=int, default=synth.WORKLOADS["batched"]["n_elements"])
     ap.add_argument("--cpu-chains", type=int, default=4096)
     ap.add_argument("--cpu-steps", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -558,34 +558,11 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         tab[NP] = zero;
     }
 
-    for (int s = 0; s < nsteps_; ++s) {
-        const uint32_t t = t0lo + (uint32_t)s;
-        if (FLOW && s >= next_from) {
-            while (ki + 1 < a.n_kap && t0_ + s >= a.kap_from[ki + 1]) ++ki;
-            kap_nz = false;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                kap[i] = T(a.kap[ki * 9 + i]);
-                kap_nz |= (kap[i] != T(0));
-            }
-            next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
-        }
-        if (WIN && a.snapR != nullptr && live) {
-            const long long sr = (long long)t0_ + s - a.snap_t0;
-            if (sr >= 0 && sr <= a.snap_steps) snapshot_store<T, W, B>(a, sr, mm, ll, R, A, S, Z);
-        }
-        const long long trow = (long long)t0_ + s - a.tape_t0;
-        const bool tape_row = WIN && tmode != 0 && live && trow >= 0 && trow < a.tape_rows;
-        uint8_t tb[B];
-#pragma unroll
-        for (int b = 0; b < B; ++b)
-            tb[b] = (tmode == 2 && tape_row) ? a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] : (uint8_t)0;
-        // ---- per-bead slot masks for this step's spring forces
-#pragma unroll
-        for (int b = 0; b < B; ++b) msk[ll + b * W] = Mask(0);
-        // ---- random numbers of this step: block (i, t, STEP, chain) per bead/slot i
-        T nrm[B][4], u[B];
-        const unsigned long long p_shared = philox_step_shared(t, kPurposeStep, c.rk0);
+    // Random numbers of step tt: block (i, tt, STEP, chain) per bead/slot i.
+    // They do not depend on the state, so each step draws the next step's
+    // at its end, where their integer work interleaves with the stress.
+    auto draw = [&](const uint32_t tt, T (&nrm)[B][4], T (&u)[B]) {
+        const unsigned long long p_shared = philox_step_shared(tt, kPurposeStep, c.rk0);
         if constexpr (PK) {
 #pragma unroll
             for (int b = 0; b < B; b += 2) {
@@ -613,6 +590,34 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 u[b] = uniform_lo24<T>(w);
             }
         }
+    };
+    T nrm[B][4], u[B];
+    draw(t0lo, nrm, u);
+    for (int s = 0; s < nsteps_; ++s) {
+        const uint32_t t = t0lo + (uint32_t)s;
+        if (FLOW && s >= next_from) {
+            while (ki + 1 < a.n_kap && t0_ + s >= a.kap_from[ki + 1]) ++ki;
+            kap_nz = false;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                kap[i] = T(a.kap[ki * 9 + i]);
+                kap_nz |= (kap[i] != T(0));
+            }
+            next_from = (ki + 1 < a.n_kap) ? rel(a.kap_from[ki + 1]) : never;
+        }
+        if (WIN && a.snapR != nullptr && live) {
+            const long long sr = (long long)t0_ + s - a.snap_t0;
+            if (sr >= 0 && sr <= a.snap_steps) snapshot_store<T, W, B>(a, sr, mm, ll, R, A, S, Z);
+        }
+        const long long trow = (long long)t0_ + s - a.tape_t0;
+        const bool tape_row = WIN && tmode != 0 && live && trow >= 0 && trow < a.tape_rows;
+        uint8_t tb[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            tb[b] = (tmode == 2 && tape_row) ? a.tape[((size_t)trow * a.M + mm) * NP + ll + b * W] : (uint8_t)0;
+        // ---- per-bead slot masks for this step's spring forces
+#pragma unroll
+        for (int b = 0; b < B; ++b) msk[ll + b * W] = Mask(0);
         __syncwarp();
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -987,6 +992,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             Z = Znew;
         }
         }  // candidates
+        draw(t + 1u, nrm, u);  // the next step's random numbers
 #pragma unroll
         for (int b = 0; b < B; ++b)
 #pragma unroll
@@ -1022,10 +1028,12 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         if (do_log) next_log += a.log_every;
         const bool do_rc = (s == next_rc) && kap_nz;
         if (s == next_rc) next_rc += a.recenter_every;
-        if (corr_on || do_log) {
-            // per-lane parts of sigma_ab (bonds) and sigma_ab + sigma^(v)_ab
-            T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-            T dgp[3] = {T(0), T(0), T(0)};
+        // per-lane parts of the off-diagonal sigma_ab (bonds) and sigma_ab +
+        // sigma^(v)_ab (v[0..5]), and with `diag` the bond part of sigma_aa
+        auto stress_parts = [&](T (&v)[8], T (&dgp)[3], const bool diag) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = T(0);
+            dgp[0] = dgp[1] = dgp[2] = T(0);
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 const int i = ll + b * W;
@@ -1061,7 +1069,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                         v[5] += kd1 * dd[b][2];
                     }
                 }
-                if (do_log) {
+                if (diag) {
                     dgp[0] += kq0 * q[0];
                     dgp[1] += kq1 * q[1];
                     dgp[2] += c.k_b * q[2] * q[2];
@@ -1070,28 +1078,37 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             v[3] += v[0];
             v[4] += v[1];
             v[5] += v[2];
+        };
+        if (corr_on) {  // every step: the correlator's input
+            T v[8], dgp[3];
+            stress_parts(v, dgp, false);
             const T red = seg_reduce8<T, W>(v, ll);
-            if (ser_m != nullptr) ser_m[(size_t)s * ser_step] = red;  // the correlator's input
-            if (do_log) {
-                T sig[3], dg[3];
+            if (ser_m != nullptr) ser_m[(size_t)s * ser_step] = red;
+        }
+        if (do_log) {
+            // a log step (warp-uniform, every log_every steps): the stress
+            // again with its diagonal, kept out of the every-step path
+            T v[8], dgp[3];
+            stress_parts(v, dgp, true);
+            const T red = seg_reduce8<T, W>(v, ll);
+            T sig[3], dg[3];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    sig[d] = shfl(red, d * G8, W);
-                    dg[d] = seg_sum<T, W>(dgp[d]) - NkT;
-                }
-                const int slot = log_slot++;
-                if (live && ll == 0 && slot < nlog_) {
-                    double* L = slog + slot * 14;
-                    const double v6[6] = {(double)dg[0], (double)dg[1], (double)dg[2],
-                                          (double)sig[0], (double)sig[1], (double)sig[2]};
+            for (int d = 0; d < 3; ++d) {
+                sig[d] = shfl(red, d * G8, W);
+                dg[d] = seg_sum<T, W>(dgp[d]) - NkT;
+            }
+            const int slot = log_slot++;
+            if (live && ll == 0 && slot < nlog_) {
+                double* L = slog + slot * 14;
+                const double v6[6] = {(double)dg[0], (double)dg[1], (double)dg[2],
+                                      (double)sig[0], (double)sig[1], (double)sig[2]};
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        atomicAdd(L + k, v6[k]);
-                        atomicAdd(L + 6 + k, v6[k] * v6[k]);
-                    }
-                    atomicAdd(L + 12, (double)Z);
-                    atomicAdd(L + 13, (double)Z * (double)Z);
+                for (int k = 0; k < 6; ++k) {
+                    atomicAdd(L + k, v6[k]);
+                    atomicAdd(L + 6 + k, v6[k] * v6[k]);
                 }
+                atomicAdd(L + 12, (double)Z);
+                atomicAdd(L + 13, (double)Z * (double)Z);
             }
         }
         if (do_rc) {
