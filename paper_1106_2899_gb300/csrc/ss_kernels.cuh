@@ -291,7 +291,7 @@ constexpr int kChunkThreads = 128;
 
 // shared memory carve-up (bytes), identical on host and device
 struct SmemPlan {
-    int off_tab, off_pos, off_msk, off_log, total;
+    int off_tab, off_pos, off_bq, off_msk, off_log, total;
 };
 
 template <typename T>
@@ -302,6 +302,9 @@ __host__ __device__ inline SmemPlan smem_plan(int warps, int W, int B, int nlog_
     int sz = warps * (32 / W) * (W * B + 1) * (int)sizeof(SlotRec<T>);
     p.off_pos = (sz + 15) & ~15;
     sz = p.off_pos + warps * 32 * B * (int)sizeof(Pos<T>);
+    p.off_bq = (sz + 15) & ~15;
+    // per chain NP + 1 bond vectors: entry i + 1 holds bead i's, entry 0 zeros
+    sz = p.off_bq + warps * (32 / W) * (W * B + 1) * (int)sizeof(Pos<T>);
     p.off_msk = (sz + 15) & ~15;
     sz = p.off_msk + warps * 32 * B * (int)sizeof(unsigned long long);
     p.off_log = (sz + 15) & ~15;
@@ -360,6 +363,49 @@ __device__ __forceinline__ T seg_reduce8(const T (&v)[8], int ll) {
     }
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off, W);
+    return r;
+}
+
+// Sums over the W lanes of a segment of six per-lane values v[0..5]
+// (sigma_xy, sigma_xz, sigma_yz and the same components of sigma + sigma^(v))
+// by a transpose reduction: the first round splits the two tensors between
+// the lane halves, the second the xy/xz pair (yz summed on both sides), the
+// third xy-or-xz against yz; butterflies finish.  On return lane ll holds
+// the total of value seg6_value(ll).
+template <int W>
+__device__ __forceinline__ int seg6_value(int ll) {
+    const int comp = (ll & (W / 8)) ? 2 : ((ll & (W / 4)) ? 1 : 0);
+    return ((ll & (W / 2)) ? 3 : 0) + comp;
+}
+template <typename T, int W>
+__device__ __forceinline__ T seg_reduce6(const T (&v)[8], int ll) {
+    T w[3];
+    {
+        const bool hi = (ll & (W / 2)) != 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T send = hi ? v[k] : v[k + 3];
+            const T keep = hi ? v[k + 3] : v[k];
+            w[k] = keep + __shfl_xor_sync(kFull, send, W / 2, W);
+        }
+    }
+    T x, y;
+    {
+        const bool hi = (ll & (W / 4)) != 0;
+        const T send = hi ? w[0] : w[1];
+        const T keep = hi ? w[1] : w[0];
+        x = keep + __shfl_xor_sync(kFull, send, W / 4, W);
+        y = w[2] + __shfl_xor_sync(kFull, w[2], W / 4, W);
+    }
+    T r;
+    {
+        const bool hi = (ll & (W / 8)) != 0;
+        const T send = hi ? x : y;
+        const T keep = hi ? y : x;
+        r = keep + __shfl_xor_sync(kFull, send, W / 8, W);
+    }
+#pragma unroll
+    for (int off = W / 16; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off, W);
     return r;
 }
 
@@ -462,6 +508,9 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     const SmemPlan plan = smem_plan<T>(nwarps, W, B, nlog_);
     SlotRec<T>* tab = reinterpret_cast<SlotRec<T>*>(smem + plan.off_tab) + (warp * SEGS + seg) * (NP + 1);
     Pos<T>* pos = reinterpret_cast<Pos<T>*>(smem + plan.off_pos) + (warp * SEGS + seg) * NP;
+    // bond vectors Q_i = R_{i+1} - R_i of the current state, one entry up:
+    // bq[i + 1] = Q_i, bq[0] = 0 (bead 0 has no left bond)
+    Pos<T>* bq = reinterpret_cast<Pos<T>*>(smem + plan.off_bq) + (warp * SEGS + seg) * (NP + 1);
     Mask* msk = reinterpret_cast<Mask*>(smem + plan.off_msk) + (warp * SEGS + seg) * NP;
     double* slog = reinterpret_cast<double*>(smem + plan.off_log);
 
@@ -493,8 +542,9 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
     // stress series of this launch (the correlator reads it afterwards)
     T* const ser = static_cast<T*>(a.series);
     const bool corr_on = ser != nullptr;
-    const int gq = ll / G8;  // value this lane holds after seg_reduce8
-    T* const ser_m = (corr_on && live && (ll % G8) == 0 && gq < 6)
+    const int gq = seg6_value<W>(ll);  // value this lane holds after seg_reduce6
+    // one writer per value: the lowest lane of its group (yz is held twice over)
+    T* const ser_m = (corr_on && live && (ll % G8) == 0 && !((gq % 3) == 2 && (ll & (W / 4))))
                          ? ser + ((size_t)a.series_row0 * a.M + mm) * 6 + gq
                          : nullptr;
     const size_t ser_step = (size_t)a.M * 6;
@@ -556,7 +606,31 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         zero.x = zero.y = zero.z = T(0);
         zero.s = -1;
         tab[NP] = zero;
+        Pos<T> z4;
+        z4.x = z4.y = z4.z = z4.w = T(0);
+        bq[0] = z4;
     }
+    // Bond vectors of the current positions (the position table holds them):
+    // the stress of a step and the bond forces of the next step both use
+    // them.  The last bead and padding beads read themselves: Q = 0.
+    T Q[B][3];
+    auto bond_vectors = [&]() {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = ll + b * W;
+            const Pos<T> p1 = pos[i < N - 1 ? i + 1 : i];
+            Q[b][0] = p1.x - R[b][0];
+            Q[b][1] = p1.y - R[b][1];
+            Q[b][2] = p1.z - R[b][2];
+            Pos<T> qq;
+            qq.x = Q[b][0];
+            qq.y = Q[b][1];
+            qq.z = Q[b][2];
+            qq.w = T(0);
+            bq[i + 1] = qq;
+        }
+    };
+    bond_vectors();
 
     // Random numbers of step tt: block (i, tt, STEP, chain) per bead/slot i.
     // They do not depend on the state, so each step draws the next step's
@@ -629,16 +703,29 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         // Forces on positions Ro (this lane's beads; the other beads from the
         // position table) with the spring vectors of the slot table: bonds
         // k_b (R_{i-1} + R_{i+1} - 2 R_i), springs -k_s sum_{j: S_j = i} d_j.
-        auto forces = [&](T (&Fo)[B][3], const T (&Ro)[B][3]) {
+        // With bonds_from_q the bond forces come from the bond vectors of the
+        // state (this lane's Q and the left neighbour's from the table):
+        // k_b (Q_i - Q_{i-1}), the same terms as from positions.
+        auto forces = [&](T (&Fo)[B][3], const T (&Ro)[B][3], const bool bonds_from_q) {
+            if (bonds_from_q) {
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-                const int i = ll + b * W;
-                const Pos<T> pl = pos[i > 0 ? i - 1 : 0];
-                const Pos<T> pr = pos[i < N - 1 ? i + 1 : i];
-                const T Rl[3] = {pl.x, pl.y, pl.z}, Rr[3] = {pr.x, pr.y, pr.z};
-                // an end bead reads itself for its missing neighbour: that term is 0
+                for (int b = 0; b < B; ++b) {
+                    const Pos<T> qm = bq[ll + b * W];  // Q_{i-1} (0 for bead 0)
+                    const T Qm[3] = {qm.x, qm.y, qm.z};
 #pragma unroll
-                for (int d = 0; d < 3; ++d) Fo[b][d] = c.k_b * (Rl[d] - Ro[b][d]) + c.k_b * (Rr[d] - Ro[b][d]);
+                    for (int d = 0; d < 3; ++d) Fo[b][d] = c.k_b * Q[b][d] - c.k_b * Qm[d];
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    const int i = ll + b * W;
+                    const Pos<T> pl = pos[i > 0 ? i - 1 : 0];
+                    const Pos<T> pr = pos[i < N - 1 ? i + 1 : i];
+                    const T Rl[3] = {pl.x, pl.y, pl.z}, Rr[3] = {pr.x, pr.y, pr.z};
+                    // an end bead reads itself for its missing neighbour: that term is 0
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) Fo[b][d] = c.k_b * (Rl[d] - Ro[b][d]) + c.k_b * (Rr[d] - Ro[b][d]);
+                }
             }
             __syncwarp();
             bool more = false;
@@ -679,11 +766,10 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             }
         };
         T F[B][3];
-        forces(F, R);
-        // Padding beads (i >= N) are stepped like the others: they hang from
-        // bead N-1 by a one-sided bond, exert no force, carry no spring and
-        // enter no stress (their bond vector reads themselves), and they are
-        // never stored.
+        forces(F, R, true);
+        // Padding beads (i >= N) are stepped like the others: their bond
+        // vectors are zero, they exert no force, carry no spring, enter no
+        // stress and are never stored.
         T Rn[B][3];
         [[maybe_unused]] T A0[B][3];
         if constexpr (HEUN) {
@@ -784,7 +870,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             }
             __syncwarp();
             T F2[B][3];
-            forces(F2, Rn);
+            forces(F2, Rn, false);
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 const int i = ll + b * W;
@@ -1023,6 +1109,10 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             }
         }
 
+        // ---- bond vectors of the new state: this step's stress, the next
+        // step's bond forces
+        bond_vectors();
+
         // ---- stress of the new state (Eq. stress_tensor_single_chain, App. B)
         const bool do_log = (s == next_log);
         if (do_log) next_log += a.log_every;
@@ -1036,10 +1126,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             dgp[0] = dgp[1] = dgp[2] = T(0);
 #pragma unroll
             for (int b = 0; b < B; ++b) {
-                const int i = ll + b * W;
-                const Pos<T> p1 = pos[i < N - 1 ? i + 1 : i];
-                // the last bead reads itself (q = 0)
-                const T q[3] = {p1.x - R[b][0], p1.y - R[b][1], p1.z - R[b][2]};
+                const T (&q)[3] = Q[b];  // the last bead's is 0
                 T kq0, kq1;
                 if constexpr (std::is_same<T, float>::value) {  // (xy, xz) as a packed pair
                     const float2 kq = __fmul2_rn(pk(c.k_b), pk(q[0], q[1]));
@@ -1082,7 +1169,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         if (corr_on) {  // every step: the correlator's input
             T v[8], dgp[3];
             stress_parts(v, dgp, false);
-            const T red = seg_reduce8<T, W>(v, ll);
+            const T red = seg_reduce6<T, W>(v, ll);
             if (ser_m != nullptr) ser_m[(size_t)s * ser_step] = red;
         }
         if (do_log) {
@@ -1090,11 +1177,11 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             // again with its diagonal, kept out of the every-step path
             T v[8], dgp[3];
             stress_parts(v, dgp, true);
-            const T red = seg_reduce8<T, W>(v, ll);
+            const T red = seg_reduce6<T, W>(v, ll);
             T sig[3], dg[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                sig[d] = shfl(red, d * G8, W);
+                sig[d] = shfl(red, d == 0 ? 0 : (d == 1 ? W / 4 : W / 8), W);
                 dg[d] = seg_sum<T, W>(dgp[d]) - NkT;
             }
             const int slot = log_slot++;
@@ -1136,10 +1223,11 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 pn.w = T(0);
                 pos[i] = pn;
             }
-            // the spring vectors from the shifted coordinates, as a launch
-            // starting here computes them: results do not depend on where the
-            // launches end
+            // the spring and bond vectors from the shifted coordinates, as a
+            // launch starting here computes them: results do not depend on
+            // where the launches end
             __syncwarp();
+            bond_vectors();
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 const int i = ll + b * W;
