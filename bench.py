@@ -21,6 +21,7 @@ Further blocks of the JSON line (outside the timed region):
              graph-replayed persistent launch per chunk: bead-steps/s from
              CUDA events over --batched-steps steps, its ALU roofline and the
              ratio to the plain per-ensemble form.
+  heun       the benchmark workload with the stochastic Heun integrator.
   precision  error of the FP32 library against the FP64 oracle per output:
              G(t) AUTO/CROSS/TOTAL at long lags and eta+(t), N1, <Z> at the 8
              startup-shear rates against the stored oracle reference
@@ -54,9 +55,9 @@ import synth  # noqa: E402
 LANES_PER_SM = 128  # FP32/INT32 lanes of a Blackwell SM: 4 schedulers x 32, one instruction per clock each
 ALG_OPS_FILE = os.path.join(ROOT, "tests", "golden", "alg_ops.txt")
 # DRAM bytes (read + write) of one chain-kernel launch of 1024 steps, per chain, from the ncu
-# capture of 16384 chains x 1024 steps summarised in profiles/ (every term scales with the chain
-# count); None until the current kernel has been captured
-TRAFFIC_BYTES_PER_CHAIN_1024 = None
+# capture of 16384 chains x 1024 steps of the current kernel (379.6 MB; every term scales with
+# the chain count), profiles/chunk_kernel_16x2_lve_small.md; None once the kernel has changed
+TRAFFIC_BYTES_PER_CHAIN_1024 = 379.6e6 / 16384
 
 
 def alg_ops():
@@ -346,6 +347,7 @@ def run_ours(args):
                              pin_memory=True).numpy()
         pinned[...] = v
         host_state[k] = pinned
+    ge.set_state(host_state)  # warm-up of the path: its staging buffer is allocated here, untimed
     ge.run(spc)
     ge.correlator("total")
     torch.cuda.synchronize()
@@ -364,6 +366,27 @@ def run_ours(args):
     h2d = M * (N * 3 * 8 + zm * 3 * 8 + zm * 4 + 4)
     d2h = 32 * w["levels"] * 96 * 8 + 4
     ge.close()
+
+    # ---------------- the same workload with the stochastic Heun integrator
+    heun = None
+    if not args.no_heun:
+        gh = SlipSpring([(M, N)], precision="fp32", seed=w["seed"], stream=stream.cuda_stream, chain_offset=rank * M)
+        gh.set_params(**synth.PAPER, corr_levels=w["levels"], groups=32, chunk_steps=args.chunk, integrator=1)
+        gh.run(0)
+        gh.run(spc)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            gh.run(spc)
+        b.record(stream)
+        torch.cuda.synchronize()
+        heun_ms = _max_over_ranks(a.elapsed_time(b), ws)
+        heun_value = float(M) * N * spc * 3 * ws / (heun_ms / 1e3)
+        heun = {"value": heun_value, "unit": "bead-steps/s", "steps": 3 * spc,
+                "form": "stochastic Heun integrator (integrator = SS_HEUN), same workload and launch shape",
+                "over_euler": heun_value / value}
+        gh.close()
 
     batched = None if args.no_batched else run_batched(args, stream, rank, sms, ops)
     precision = None if (args.no_precision or rank != 0) else run_precision(stream)
@@ -396,6 +419,7 @@ def run_ours(args):
                   "batched_over_plain": value / plain_value},
         "e2e": {"value": e2e_value, "unit": "bead-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "heun": heun,
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-ops/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -517,6 +541,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-heun", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -286,8 +286,8 @@ constexpr int kChunkThreads = 128;
 #define SS_CTAS_PER_SM_MULTI 5  // for layouts with several beads per lane
 #endif
 #ifndef SS_CTAS_PER_SM_BATCHED_MULTI
-#define SS_CTAS_PER_SM_BATCHED_MULTI 4  // the batched kernel reads its arguments through a pointer
-#endif
+#define SS_CTAS_PER_SM_BATCHED_MULTI 4  // the batched kernel with 3 or more beads per lane (it reads its
+#endif                                  // arguments through a pointer; 2 beads per lane fit 5 CTAs/SM)
 
 // shared memory carve-up (bytes), identical on host and device
 struct SmemPlan {
@@ -1336,7 +1336,7 @@ struct RunInfo {
 };
 
 template <typename T, int W, int B>
-__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : SS_CTAS_PER_SM_BATCHED_MULTI)
+__global__ void __launch_bounds__(kChunkThreads, B == 1 ? SS_CTAS_PER_SM : (B == 2 ? SS_CTAS_PER_SM_MULTI : SS_CTAS_PER_SM_BATCHED_MULTI))
     batched_kernel(const ChunkArgs* __restrict__ elems, const int2* __restrict__ items, int n_items,
                    unsigned* __restrict__ next_item, const RunInfo info, const StepConst<T> c) {
     __shared__ int item_s;
