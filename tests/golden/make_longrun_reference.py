@@ -12,6 +12,9 @@ state of Sec. 3.1:
   (Eq. relaxation_modulus_tensor_green_kubo_form with the virtual stress of
   App. B; averaged over xy, xz, yz; in rho0 kT, i.e. divided by N kT^2) with
   their standard errors over 32 chain groups.  -> longrun_G_oracle.txt
+* The same equilibrium G(t) with the stochastic Heun integrator (integrator =
+  1; Sec. 3.1's stochastic Runge-Kutta alternative): N = 32, 2048 chains (seed
+  62), 20000 + 320000 steps.  -> longrun_G_heun_oracle.txt
 * Startup shear (Sec. 4.1, viscosity growth): N = 32, 1024 chains per rate
   (seeds 71 + k), kappa_xy = gdot from step 0 for the 8 rates
   10^(-4 + 3k/7), 200000 steps, stress logged every 100 steps.  At about 100
@@ -39,6 +42,7 @@ import oracle  # noqa: E402
 import synth  # noqa: E402
 
 G_SPEC = dict(N=32, M=2048, seed=61, equil=20000, steps=320000, levels=24, groups=32)
+G_HEUN_SPEC = dict(G_SPEC, seed=62, integrator=1)
 ETA_SPEC = dict(N=32, M=1024, seed0=71, steps=200000, log_every=100, groups=32,
                 rates=[10 ** (-4 + 3 * k / 7) for k in range(8)])
 
@@ -50,7 +54,7 @@ def log_times(n_logs, n_pick=100):
 
 
 def make_G(spec, out_path, nthreads=0):
-    p = oracle.Params(N=spec["N"], **synth.PAPER)
+    p = oracle.Params(N=spec["N"], integrator=spec.get("integrator", 0), **synth.PAPER)
     M, G, L = spec["M"], spec["groups"], spec["levels"]
     e = oracle.Ensemble(p, seed=spec["seed"], M=M, groups=G, levels=L)
     e.init()
@@ -76,6 +80,8 @@ def make_G(spec, out_path, nthreads=0):
     rows.sort(key=lambda r: r[0])
     with open(out_path, "w") as f:
         f.write("# FP64 oracle relaxation modulus, equilibrium (Eq. relaxation_modulus_tensor_green_kubo_form,\n")
+        if spec.get("integrator", 0):
+            f.write("# stochastic Heun integrator\n")
         f.write("# App. B virtual stress), written by tests/golden/make_longrun_reference.py\n")
         f.write("# spec %r\n" % (spec,))
         f.write("# lag_steps G_auto se_auto G_cross se_cross G_total se_total  (rho0 kT; SE over %d groups)\n" % G)
@@ -125,7 +131,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
-    ap.add_argument("--only", choices=["G", "eta"], default=None)
+    ap.add_argument("--only", choices=["G", "eta", "heun"], default=None)
     a = ap.parse_args()
     gs, es, out = dict(G_SPEC), dict(ETA_SPEC), HERE
     if a.quick:
@@ -137,6 +143,12 @@ def main():
     if a.only in (None, "G"):
         make_G(gs, os.path.join(out, "longrun_G_oracle.txt"), a.threads)
         print("G done %.0f s" % (time.time() - t), flush=True)
+    if a.only in (None, "heun"):
+        hs = dict(G_HEUN_SPEC)
+        if a.quick:
+            hs.update(M=64, equil=100, steps=2000)
+        make_G(hs, os.path.join(out, "longrun_G_heun_oracle.txt"), a.threads)
+        print("heun G done %.0f s" % (time.time() - t), flush=True)
     if a.only in (None, "eta"):
         make_eta(es, os.path.join(out, "longrun_eta_oracle.txt"), a.threads)
         print("eta done %.0f s" % (time.time() - t), flush=True)

@@ -7,6 +7,7 @@ The library runs the same workloads with more chains and its own seeds:
   320000 steps into the 16 x 24 multiple-tau correlator; AUTO, CROSS and TOTAL
   channels (Eq. relaxation_modulus_tensor_green_kubo_form, App. B) with
   standard errors over 32 chain groups, read through ss_correlator.
+  The same with the stochastic Heun integrator against its own reference.
 * Startup shear (Sec. 4.1), N = 32: 16384 chains per rate, the 8 rates
   10^(-4 + 3k/7), 200000 steps, stress logs every 100 steps; eta+ =
   <sigma_xy>/(N gdot), N1 = <sigma_xx - sigma_yy> and <Z> per log from the
@@ -31,6 +32,7 @@ import synth
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 G_FILE = os.path.join(GOLDEN, "longrun_G_oracle.txt")
+G_HEUN_FILE = os.path.join(GOLDEN, "longrun_G_heun_oracle.txt")
 ETA_FILE = os.path.join(GOLDEN, "longrun_eta_oracle.txt")
 CHANNELS = ("auto", "cross", "total")
 
@@ -60,10 +62,10 @@ def load_eta(path=ETA_FILE):
     return steady, {k: np.array(v) for k, v in logs.items()}
 
 
-def gpu_G(M=65536, N=32, seed=5, equil=20000, steps=320000, levels=24, groups=32, stream=None):
+def gpu_G(M=65536, N=32, seed=5, equil=20000, steps=320000, levels=24, groups=32, stream=None, integrator=0):
     from paper_1106_2899_gb300 import SlipSpring
     g = SlipSpring([(M, N)], precision="fp32", seed=seed, stream=stream)
-    g.set_params(corr_levels=levels, groups=groups, **synth.PAPER)
+    g.set_params(corr_levels=levels, groups=groups, integrator=integrator, **synth.PAPER)
     g.run(0)
     g.run(equil)
     g.reset_observables()

@@ -4,6 +4,8 @@ tests/golden/make_longrun_reference.py from independent oracle ensembles).
 
 * G(t) in equilibrium, N = 32, 320000 steps: the AUTO, CROSS and TOTAL
   channels at every multiple-tau lag up to beyond 1e5 steps.
+* The same G(t) with the stochastic Heun integrator, against an oracle
+  ensemble run with the Heun integrator.
 * Startup shear at the 8 rates 1e-4 .. 1e-1 over 200000 steps: eta+(t), the
   first normal stress difference and <Z> at about 100 log-spaced times per
   rate, and the steady viscosity per rate.
@@ -33,6 +35,19 @@ def test_relaxation_modulus_channels_to_long_lags(cuda_ok):
         allz += r["zs"]
     assert lp.passes(allz, []), sorted(allz)[-10:]
     # the short lags are resolved: the 2% bound is exercised there
+    assert res["total"]["resolved_lags"] >= 10 and res["auto"]["resolved_lags"] >= 10
+
+
+def test_relaxation_modulus_heun_integrator(cuda_ok):
+    ref = lp.load_G(lp.G_HEUN_FILE)
+    res = lp.compare_G(lp.gpu_G(seed=6, integrator=1), ref)
+    allz = []
+    for ch, r in res.items():
+        assert r["max_lag_steps"] >= 100000, (ch, r["max_lag_steps"])
+        assert r["lags_compared"] >= 120, (ch, r["lags_compared"])
+        assert not r["failures"], (ch, r["failures"][:5])
+        allz += r["zs"]
+    assert lp.passes(allz, []), sorted(allz)[-10:]
     assert res["total"]["resolved_lags"] >= 10 and res["auto"]["resolved_lags"] >= 10
 
 
