@@ -539,6 +539,17 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         pos[i] = p0;
     }
 
+    // creation attempts at the current Z (substep 3a): slots first = Z ..
+    // c_last - 1 attempt, each creating with probability p_c(K = c_last - Z) at
+    // either end; kept here because they change only with Z
+    int c_last = Z;
+    T c_pc2 = T(0);  // 2 p_c
+    auto set_create = [&]() {
+        c_last = Z < a.zmax ? ((a.create_mode == 0) ? a.zmax : Z + 1) : Z;
+        c_pc2 = T(2) * c.pc[c_last - Z];
+    };
+    set_create();
+
     // stress series of this launch (the correlator reads it afterwards)
     T* const ser = static_cast<T*>(a.series);
     const bool corr_on = ser != nullptr;
@@ -954,11 +965,9 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 
         // ---- substep 3a: creation, K attempts at both ends
         const int Zc = Z;
-        int first = Zc, last = Zc;
-        if (Zc < a.zmax) last = (a.create_mode == 0) ? a.zmax : Zc + 1;
+        const int first = Zc, last = c_last;
         if (Zc >= a.zmax && a.create_mode == 1 && ll == 0 && live) ++cnt_drop;
-        const int K = last - first;
-        const T pc = c.pc[K];
+        const T pc = T(0.5) * c_pc2;
         // a slot can change only if it may create (u < 2 p_c on an attempt) or
         // sits at an end with a destruction hit: the detailed work below runs
         // only when some slot of the warp can
@@ -966,7 +975,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
-            cand |= ((i >= first) && (i < last) && (u[b] < T(2) * pc)) ||
+            cand |= ((i >= first) && (i < last) && (u[b] < c_pc2)) ||
                     ((i < Zc) && (S[b] == 0 || S[b] == N - 1) && (nrm[b][3] < c.cd));
         }
         if (__any_sync(kFull, cand)) {
@@ -976,7 +985,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         for (int b = 0; b < B; ++b) {
             const int i = ll + b * W;
             const bool att = (i >= first) && (i < last);
-            end_new[b] = !att ? -1 : (u[b] < pc ? 0 : (u[b] < T(2) * pc ? N - 1 : -1));
+            end_new[b] = !att ? -1 : (u[b] < pc ? 0 : (u[b] < c_pc2 ? N - 1 : -1));
             if (tmode == 2) end_new[b] = !att ? -1 : ((tb[b] & kTapeNew0) ? 0 : ((tb[b] & kTapeNewN) ? N - 1 : -1));
             if (tmode == 1) tb[b] |= end_new[b] == 0 ? kTapeNew0 : (end_new[b] > 0 ? kTapeNewN : 0);
             any_new |= end_new[b] >= 0;
@@ -1076,6 +1085,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
             }
             __syncwarp();
             Z = Znew;
+            set_create();
         }
         }  // candidates
         draw(t + 1u, nrm, u);  // the next step's random numbers
