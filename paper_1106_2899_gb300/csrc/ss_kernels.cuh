@@ -539,12 +539,18 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         pos[i] = p0;
     }
 
-    // creation attempts at the current Z (substep 3a): slots first = Z ..
-    // c_last - 1 attempt, each creating with probability p_c(K = c_last - Z) at
-    // either end; kept here because they change only with Z
+    // Values that change only with Z, kept from one change to the next: the
+    // creation attempts of substep 3a (slots first = Z .. c_last - 1, each
+    // creating with probability p_c(K = c_last - Z) at either end; c_drop: an
+    // attempt dropped at the cap, counted on lane 0) and the largest Z of this
+    // warp's chains (sub-slots at or above it hold no spring).
     int c_last = Z;
     T c_pc2 = T(0);  // 2 p_c
+    int z_w = 0;
+    bool c_drop = false;
     auto set_create = [&]() {
+        c_drop = Z >= a.zmax && a.create_mode == 1 && ll == 0 && live;
+        z_w = (int)__reduce_max_sync(kFull, (unsigned)Z);
         c_last = Z < a.zmax ? ((a.create_mode == 0) ? a.zmax : Z + 1) : Z;
         c_pc2 = T(2) * c.pc[c_last - Z];
     };
@@ -922,7 +928,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
 
         // ---- substep 2: hops on the new positions, one uniform per spring;
         // sub-slots above every chain's Z in this warp are skipped
-        const int zw = (int)__reduce_max_sync(kFull, (unsigned)Z);
+        const int zw = z_w;
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             if (b * W >= zw) break;
@@ -966,7 +972,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         // ---- substep 3a: creation, K attempts at both ends
         const int Zc = Z;
         const int first = Zc, last = c_last;
-        if (Zc >= a.zmax && a.create_mode == 1 && ll == 0 && live) ++cnt_drop;
+        if (c_drop) ++cnt_drop;
         const T pc = T(0.5) * c_pc2;
         // a slot can change only if it may create (u < 2 p_c on an attempt) or
         // sits at an end with a destruction hit: the detailed work below runs
@@ -1097,7 +1103,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         // ---- spring vectors of the new state, d_j = R_{S_j} - A_j (0 for an
         // empty slot): next step's spring forces and this step's stress;
         // sub-slots above every chain's Z in this warp hold none
-        const int zn = (int)__reduce_max_sync(kFull, (unsigned)Z);
+        const int zn = z_w;
         T dd[B][3];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
