@@ -914,7 +914,10 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 }
             }
         }
-        __syncwarp();
+        // the Heun corrector read positions of other lanes just above; without
+        // it the last reads of the position table lie behind the barriers of
+        // the slot masks and of the forces
+        if constexpr (HEUN) __syncwarp();
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             Pos<T> pn;
@@ -999,7 +1002,8 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
         T Anew[B][3];
 #pragma unroll
         for (int b = 0; b < B; ++b) Anew[b][0] = Anew[b][1] = Anew[b][2] = T(0);
-        if (__any_sync(kFull, any_new)) {
+        const bool some_new = __any_sync(kFull, any_new);
+        if (some_new) {
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 if (end_new[b] >= 0) {
@@ -1050,6 +1054,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 dest[b] = alive_old[b] ? base + __popc(kb & lt) : -1;
                 base += __popc(kb);
             }
+            if (some_new) {  // new springs in this warp: at bead 1, then at bead N
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 const bool e0 = alive_new[b] && end_new[b] == 0;
@@ -1063,6 +1068,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 const unsigned nb = __ballot_sync(kFull, eN) & segmask;
                 if (eN) dest[b] = base + __popc(nb & lt);
                 base += __popc(nb);
+            }
             }
             const int Znew = base;
             __syncwarp();
