@@ -122,8 +122,12 @@ struct Mth;
 template <>
 struct Mth<float> {
     static __device__ __forceinline__ float neg2log(float x) { return __log2f(x) * -1.3862943611198906f; }
-    // sqrt of x >= 0 as x / sqrt(x); x = 0 gives 0
-    static __device__ __forceinline__ float sqrt(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
+    // sqrt of x >= 0 by the hardware approximation (sqrt.approx); x = 0 gives 0
+    static __device__ __forceinline__ float sqrt(float x) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
     static __device__ __forceinline__ void sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
     static __device__ __forceinline__ float exp(float x) { return __expf(x); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
@@ -184,7 +188,7 @@ __device__ __forceinline__ void box_muller_x2(uint32_t a0, uint32_t b0, uint32_t
                                               float& s0, float& c1, float& s1) {
     const float2 v = __fmul2_rn(pk(float((a0 >> 8) + 1u), float((a1 >> 8) + 1u)), pk(1.0f / 16777216.0f));
     const float2 m = __fmul2_rn(pk(__log2f(v.x), __log2f(v.y)), pk(-1.3862943611198906f));
-    const float2 r = __fmul2_rn(m, pk(rsqrtf(fmaxf(m.x, 1e-30f)), rsqrtf(fmaxf(m.y, 1e-30f))));
+    const float2 r = pk(Mth<float>::sqrt(m.x), Mth<float>::sqrt(m.y));
     const float2 th = __fmul2_rn(pk(float(int(b0 >> 8) - (1 << 23)), float(int(b1 >> 8) - (1 << 23))),
                                  pk(3.14159265358979323846f / 8388608.0f));
     float sa, ca, sb, cb;
