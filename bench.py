@@ -56,9 +56,9 @@ import synth  # noqa: E402
 LANES_PER_SM = 128  # FP32/INT32 lanes of a Blackwell SM: 4 schedulers x 32, one instruction per clock each
 ALG_OPS_FILE = os.path.join(ROOT, "tests", "golden", "alg_ops.txt")
 # DRAM bytes (read + write) of one chain-kernel launch of 1024 steps, per chain, from the ncu
-# capture of 16384 chains x 1024 steps of the current kernel (382.6 MB; every term scales with
+# capture of 16384 chains x 1024 steps of the current kernel (382.8 MB; every term scales with
 # the chain count), profiles/chunk_kernel_16x2_lve_small.md; None once the kernel has changed
-TRAFFIC_BYTES_PER_CHAIN_1024 = 382.6e6 / 16384
+TRAFFIC_BYTES_PER_CHAIN_1024 = 382.8e6 / 16384
 
 
 def alg_ops():

@@ -218,7 +218,8 @@ def _first_tie(margins):
     return first
 
 
-@pytest.mark.parametrize("N,kappa", [(32, None), (16, None), (24, 0.05), (48, None), (80, 0.02)])
+@pytest.mark.parametrize("N,kappa", [(32, None), (16, None), (24, 0.05), (48, None), (80, 0.02), (128, None),
+                                     (11, 0.03), (2, None)])
 def test_fp32_stepwise_parity_until_near_tie(N, kappa):
     p = Params(N=N, z_max=min(N, 64))
     M = 512 if N > 16 else 1024
