@@ -359,6 +359,8 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         win ? ssk::chunk_kernel<T, W, B, true, true> : ssk::chunk_kernel<T, W, B, false, true>;
     if (c->P.integrator == SS_HEUN) {
         kern = ssk::chunk_kernel<T, W, B, false, true, true>;  // windows refuse this integrator
+        if constexpr (std::is_same<T, float>::value)
+            if (!flow_in_window(e, t0, nsteps)) kern = ssk::chunk_kernel<T, W, B, false, false, true>;
     } else if constexpr (std::is_same<T, float>::value) {
         if (!win && !flow_in_window(e, t0, nsteps)) kern = ssk::chunk_kernel<T, W, B, false, false>;
     }
