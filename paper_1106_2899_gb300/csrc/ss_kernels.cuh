@@ -918,9 +918,10 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 }
             }
         }
-        // the Heun corrector read positions of other lanes just above; without
-        // it the last reads of the position table lie behind the barriers of
-        // the slot masks and of the forces
+        // the Heun corrector above read other lanes' positions, so they are
+        // overwritten only after a barrier; in the Euler step the last reads
+        // of the position table lie behind the barriers of the slot masks and
+        // of the forces already
         if constexpr (HEUN) __syncwarp();
 #pragma unroll
         for (int b = 0; b < B; ++b) {
