@@ -362,7 +362,8 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
         if constexpr (std::is_same<T, float>::value)
             if (!flow_in_window(e, t0, nsteps)) kern = ssk::chunk_kernel<T, W, B, false, false, true>;
     } else if constexpr (std::is_same<T, float>::value) {
-        if (!win && !flow_in_window(e, t0, nsteps)) kern = ssk::chunk_kernel<T, W, B, false, false>;
+        if (!flow_in_window(e, t0, nsteps))
+            kern = win ? ssk::chunk_kernel<T, W, B, true, false> : ssk::chunk_kernel<T, W, B, false, false>;
     }
     // the attribute belongs to the current device: set it on every launch that
     // needs more than the default 48 KiB (a host call per launch of many steps)
