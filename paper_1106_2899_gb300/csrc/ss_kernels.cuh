@@ -330,46 +330,6 @@ __device__ __forceinline__ T seg_sum(T v) {
     return v;
 }
 
-// Sums of eight per-lane values over the W lanes of a segment by a transpose
-// reduction: the first three exchange rounds halve the number of values each
-// lane carries (a lane keeps one half and sends the other), the remaining
-// rounds are plain butterflies.  On return lane ll holds the total of value
-// (ll / (W/8)) & 7.
-template <typename T, int W>
-__device__ __forceinline__ T seg_reduce8(const T (&v)[8], int ll) {
-    constexpr int G = W / 8;
-    T w4[4];
-    {
-        const bool hi = (ll & (W / 2)) != 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T send = hi ? v[k] : v[k + 4];
-            const T keep = hi ? v[k + 4] : v[k];
-            w4[k] = keep + __shfl_xor_sync(kFull, send, W / 2, W);
-        }
-    }
-    T w2[2];
-    {
-        const bool hi = (ll & (W / 4)) != 0;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const T send = hi ? w4[k] : w4[k + 2];
-            const T keep = hi ? w4[k + 2] : w4[k];
-            w2[k] = keep + __shfl_xor_sync(kFull, send, W / 4, W);
-        }
-    }
-    T r;
-    {
-        const bool hi = (ll & (W / 8)) != 0;
-        const T send = hi ? w2[0] : w2[1];
-        const T keep = hi ? w2[1] : w2[0];
-        r = keep + __shfl_xor_sync(kFull, send, W / 8, W);
-    }
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off, W);
-    return r;
-}
-
 // Sums over the W lanes of a segment of six per-lane values v[0..5]
 // (sigma_xy, sigma_xz, sigma_yz and the same components of sigma + sigma^(v))
 // by a transpose reduction: the first round splits the two tensors between
@@ -489,7 +449,7 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                                            const long long log_m0_, const int nlog_) {
     constexpr int SEGS = 32 / W;
     constexpr int NP = W * B;
-    constexpr int G8 = W / 8;        // lanes per value group after seg_reduce8
+    constexpr int G8 = W / 8;        // lanes per value group after seg_reduce6
     constexpr bool PK = std::is_same<T, float>::value && (B % 2) == 0;  // packed FP32x2 bead pairs
     // per-bead slot masks: 32 bits cover every slot when NP <= 32
     using Mask = typename std::conditional<(NP <= 32), unsigned, unsigned long long>::type;
