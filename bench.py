@@ -512,16 +512,20 @@ def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return None
-    vals = []
+    vals, secs = [], []
     cb = None
     for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
         cb = cpu_baseline(args.cpu_chains, max(50, args.cpu_steps // 5))
+        dt = time.perf_counter() - t
         cb.pop("_G")
         if k >= args.warmup:
             vals.append(cb["value"])
+            secs.append(dt)
     value = float(np.mean(vals))
     return {"impl": "reference", "metric": "bead-steps/s", "value": value, "unit": "bead-steps/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "lve: 65536 chains x N=32 (bounded sample: %d chains per step)" % args.cpu_chains},
             "cpu_baseline": {"value": value, "unit": "bead-steps/s", "cores": cb["cores"], "kind": "oracle",
