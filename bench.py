@@ -20,7 +20,9 @@ Further blocks of the JSON line (outside the timed region):
              Gaussian velocity gradients redrawn every 1000 steps) in one
              graph-replayed persistent launch per chunk: bead-steps/s from
              CUDA events over --batched-steps steps, its ALU roofline and the
-             ratio to the plain per-ensemble form.
+             ratio to the plain per-ensemble form; `n32`: the same element
+             table with every chain length 32, against the plain form at the
+             same N.
   heun       the benchmark workload with the stochastic Heun integrator.
   precision  error of the FP32 library against the FP64 oracle per output:
              G(t) AUTO/CROSS/TOTAL at long lags and eta+(t), N1, <Z> at the 8
@@ -174,18 +176,14 @@ def _peak(sms, clk):
         "the timed region), 1 lane-op per lane per clock" % (sms, LANES_PER_SM, mhz)
 
 
-def run_batched(args, stream, rank, sms, ops_by_n):
-    """The batched multiscale workload: one graph-replayed persistent launch per chunk."""
+def _time_batched(els, G, n_k, every, steps, stream, rank, seed):
+    """Run a batched ensemble (elements els, velocity-gradient table G) for 1000
+    warm-up steps, then time `steps` more with CUDA events and sampled clocks."""
     import torch
 
     from paper_1106_2899_gb300 import SlipSpring
-    w = synth.WORKLOADS["batched"]
-    warm, steps, every = 1000, args.batched_steps, w["kappa_every"]
-    n_k = (warm + steps) // every + 1
-    Ms, Ns, G = synth.element_table(args.batched_elements, seed=w["seed"], lengths=w["lengths"], m_lo=w["m_lo"],
-                                    m_hi=w["m_hi"], n_kappa=n_k, kappa_std=w["kappa_std"])
-    els = [(int(m), int(n)) for m, n in zip(Ms, Ns)]
-    g = SlipSpring(els, precision="fp32", seed=w["seed"] + 1000 * rank, stream=stream.cuda_stream)
+    warm = 1000
+    g = SlipSpring(els, precision="fp32", seed=seed + 1000 * rank, stream=stream.cuda_stream)
     g.set_params(**synth.PAPER, corr_levels=-1, groups=4, log_every=100, max_logs=(warm + steps) // 100,
                  chunk_steps=1000)
     g.set_batched(True)
@@ -207,19 +205,46 @@ def run_batched(args, stream, rank, sms, ops_by_n):
     status = g.status()
     launches = g.counters()["launches"] - c0
     g.close()
+    return ms, clk, status, launches
+
+
+def run_batched(args, stream, rank, sms, ops_by_n):
+    """The batched multiscale workload: one graph-replayed persistent launch per
+    chunk; then the same element table with every chain length set to 32 (the
+    batched form at the benchmark's N against the plain per-ensemble form)."""
+    w = synth.WORKLOADS["batched"]
+    steps, every = args.batched_steps, w["kappa_every"]
+    n_k = (1000 + steps) // every + 1
+    Ms, Ns, G = synth.element_table(args.batched_elements, seed=w["seed"], lengths=w["lengths"], m_lo=w["m_lo"],
+                                    m_hi=w["m_hi"], n_kappa=n_k, kappa_std=w["kappa_std"])
+    els = [(int(m), int(n)) for m, n in zip(Ms, Ns)]
+    ms, clk, status, launches = _time_batched(els, G, n_k, every, steps, stream, rank, w["seed"])
     beads = float(sum(m * n for m, n in els))
     ops = sum(m * n * ops_by_n["flow_%d" % n]["total"] for m, n in els) / beads
     value = beads * steps / (ms / 1e3)
     peak, basis = _peak(sms, clk)
-    return {"value": value, "unit": "bead-steps/s", "steps": steps, "ms": ms,
-            "workload": "batched multiscale: %d elements, %d chains, %.4g beads (N in %s), FP32 beads / FP64 "
-                        "per-element stress sums, kappa redrawn every %d steps" % (
-                            len(els), int(sum(Ms)), beads, list(w["lengths"]), every),
-            "roofline": {"bound": "alu", "achieved": ops * value, "peak": peak, "unit": "lane-ops/s",
-                         "frac": ops * value / peak, "alg_ops_per_bead_step": ops,
-                         "kernel": "batched_kernel (all lane-layout classes of one graph launch per chunk, "
-                                   "timed together with CUDA events)", "peak_basis": basis, "traffic": None},
-            "clocks": clk, "status": status, "gpu_launches": int(launches)}
+    out = {"value": value, "unit": "bead-steps/s", "steps": steps, "ms": ms,
+           "workload": "batched multiscale: %d elements, %d chains, %.4g beads (N in %s), FP32 beads / FP64 "
+                       "per-element stress sums, kappa redrawn every %d steps" % (
+                           len(els), int(sum(Ms)), beads, list(w["lengths"]), every),
+           "roofline": {"bound": "alu", "achieved": ops * value, "peak": peak, "unit": "lane-ops/s",
+                        "frac": ops * value / peak, "alg_ops_per_bead_step": ops,
+                        "kernel": "batched_kernel (all lane-layout classes of one graph launch per chunk, "
+                                  "timed together with CUDA events)", "peak_basis": basis, "traffic": None},
+           "clocks": clk, "status": status, "gpu_launches": int(launches)}
+    els32 = [(m, 32) for m, _ in els]
+    ms32, clk32, status32, launches32 = _time_batched(els32, G, n_k, every, steps, stream, rank, w["seed"])
+    beads32 = float(sum(m * n for m, n in els32))
+    value32 = beads32 * steps / (ms32 / 1e3)
+    ops32 = ops_by_n["flow_32"]["total"]
+    peak32, _ = _peak(sms, clk32)
+    out["n32"] = {"value": value32, "unit": "bead-steps/s", "steps": steps, "ms": ms32,
+                  "workload": "the same %d elements and velocity gradients, every chain N = 32 (%.4g beads)" % (
+                      len(els32), beads32),
+                  "roofline": {"bound": "alu", "achieved": ops32 * value32, "peak": peak32, "unit": "lane-ops/s",
+                               "frac": ops32 * value32 / peak32, "alg_ops_per_bead_step": ops32},
+                  "clocks": clk32, "status": status32, "gpu_launches": int(launches32)}
+    return out
 
 
 def run_precision(stream):
@@ -440,6 +465,7 @@ def run_ours(args):
     }
     if batched is not None:
         batched["over_plain"] = batched["value"] / plain_value
+        batched["n32"]["over_plain"] = batched["n32"]["value"] / plain_value
         out["batched"] = batched
     if precision is not None:
         out["precision"] = precision
