@@ -159,11 +159,12 @@ int ss_set_flow_table(ss_ctx* ctx, int n, const int32_t* elem, const int64_t* fr
 
 /* Batched mode (support for many elements; not in the paper): when enabled,
  * ss_run advances all elements with one persistent launch per chunk of
- * chunk_steps steps, replayed from a captured CUDA graph; CTAs take (element,
- * chain tile) work items from an atomic counter, longest chains first.  Before
- * the first batched launch an autotuner times the candidate lane layouts of
- * each chain length on a scratch ensemble and keeps the fastest (results
- * cached per process).  Batched mode keeps the stress logs, not the
+ * chunk_steps steps, replayed from an explicitly built CUDA graph; CTAs take
+ * (element, chain tile) work items from an atomic counter, longest chains
+ * first.  Before the first batched launch an autotuner times the candidate lane
+ * layouts of each chain length on a scratch ensemble and keeps the fastest (the
+ * default layout unless another is at least 3% faster; results cached per
+ * process).  Batched mode keeps the stress logs, not the
  * correlator: ss_run fails with SS_EINVAL unless corr_levels < 0.  The
  * numbers drawn and the results are those of the per-element path with the
  * same layout.  enable = 0 returns to the per-element path and its default
@@ -370,11 +371,10 @@ int ss_window_backward(ss_ctx* ctx, const double* dL_dG, double grad[3]);
  *   corr_levels; with the correlator on, at least one step of series must fit),
  *   SS_EOVERFLOW if t0 + n_steps passes 2^32, SS_ECUDA.
  * The first call on a device looks up the device address of the array (with
- *   that device current) and caches it; make that first call before any stream
- *   capture.  Every call, on any stream, uses the same array and leaves its
- *   contents behind; each call clears what must start at zero.  Calls that
- *   overlap on the GPU race on the array: serialise them (one stream, or
- *   events). */
+ *   that device current) and caches it.  Every call, on any stream, uses the
+ *   same array and leaves its contents behind; each call clears what must
+ *   start at zero.  Calls that overlap on the GPU race on the array:
+ *   serialise them (one stream, or events). */
 #define SS_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ss_run_noalloc(const ss_params* params, int precision, uint64_t seed, int32_t n_chains,
                    int32_t n_beads, uint32_t chain_base, int64_t t0, int64_t n_steps,
