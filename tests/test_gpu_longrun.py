@@ -2,8 +2,9 @@
 the FP64 oracle (GPU; the oracle side is the stored reference written by
 tests/golden/make_longrun_reference.py from independent oracle ensembles).
 
-* G(t) in equilibrium, N = 32, 320000 steps: the AUTO, CROSS and TOTAL
-  channels at every multiple-tau lag up to beyond 1e5 steps.
+* G(t) in equilibrium, N = 32, the LVE workload at its full size (65536
+  chains, 10^6 steps) against an oracle ensemble of 3.2e5 steps: the AUTO,
+  CROSS and TOTAL channels at every multiple-tau lag up to beyond 1e5 steps.
 * The same G(t) with the stochastic Heun integrator, against an oracle
   ensemble run with the Heun integrator.
 * Startup shear at the 8 rates 1e-4 .. 1e-1 over 200000 steps: eta+(t), the
@@ -26,7 +27,9 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 def test_relaxation_modulus_channels_to_long_lags(cuda_ok):
     ref = lp.load_G()
-    res = lp.compare_G(lp.gpu_G(), ref)
+    # the equilibrium LVE workload at its full size: 65536 chains, 10^6 steps
+    w = synth.WORKLOADS["lve"]
+    res = lp.compare_G(lp.gpu_G(M=w["M"], N=w["N"], steps=w["steps"], levels=w["levels"]), ref)
     allz = []
     for ch, r in res.items():
         assert r["max_lag_steps"] >= 100000, (ch, r["max_lag_steps"])
