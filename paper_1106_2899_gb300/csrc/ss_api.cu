@@ -353,14 +353,14 @@ int launch_chunk(ss_ctx* c, Elem& e, long long t0, int nsteps) {
     }
     const ssk::SmemPlan plan = ssk::smem_plan<T>(kWarpsPerCta, W, B, a.nlog_chunk);
     // differentiation windows run the instantiation with the window hooks; an
-    // FP32 launch without a velocity gradient the one without the flow terms
+    // FP32 launch without a velocity gradient, and a Heun launch without one in
+    // either precision, the one without the flow terms
     const bool win = c->opt_tape_mode != 0 || c->opt_snap;
     void (*kern)(const ssk::ChunkArgs, const ssk::StepConst<T>) =
         win ? ssk::chunk_kernel<T, W, B, true, true> : ssk::chunk_kernel<T, W, B, false, true>;
     if (c->P.integrator == SS_HEUN) {
         kern = ssk::chunk_kernel<T, W, B, false, true, true>;  // windows refuse this integrator
-        if constexpr (std::is_same<T, float>::value)
-            if (!flow_in_window(e, t0, nsteps)) kern = ssk::chunk_kernel<T, W, B, false, false, true>;
+        if (!flow_in_window(e, t0, nsteps)) kern = ssk::chunk_kernel<T, W, B, false, false, true>;
     } else if constexpr (std::is_same<T, float>::value) {
         if (!flow_in_window(e, t0, nsteps))
             kern = win ? ssk::chunk_kernel<T, W, B, true, false> : ssk::chunk_kernel<T, W, B, false, false>;

@@ -321,6 +321,9 @@ __host__ __device__ inline SmemPlan smem_plan(int warps, int W, int B, int nlog_
 // 1 + index of the lowest set bit (0 for none) of a 32- or 64-bit slot mask
 __device__ __forceinline__ int mask_ffs(unsigned m) { return __ffs((int)m); }
 __device__ __forceinline__ int mask_ffs(unsigned long long m) { return __ffsll((long long)m); }
+// number of set bits of a slot mask
+__device__ __forceinline__ int mask_popc(unsigned m) { return __popc(m); }
+__device__ __forceinline__ int mask_popc(unsigned long long m) { return __popcll(m); }
 
 // Sum over the W lanes of a segment; every lane of the segment gets the sum.
 template <typename T, int W>
@@ -819,7 +822,42 @@ __device__ __forceinline__ void run_chains(const ChunkArgs& a, const StepConst<T
                 for (int d = 0; d < 3; ++d) A[b][d] = An[d];
             }
         }
-        if constexpr (HEUN) {
+        if constexpr (HEUN && !FLOW) {
+            // Stochastic Heun corrector without a velocity gradient: the
+            // anchors stay where they are, so the springs' force at the
+            // predicted positions is the step's spring force less
+            // k_s n_i (Rn_i - R_i), n_i the number of springs on bead i (the
+            // same sum, reordered); only the bond forces are recomputed.
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                Pos<T> pn;
+                pn.x = Rn[b][0];
+                pn.y = Rn[b][1];
+                pn.z = Rn[b][2];
+                pn.w = T(0);
+                pos[ll + b * W] = pn;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int i = ll + b * W;
+                const Pos<T> pl = pos[i > 0 ? i - 1 : 0];
+                const Pos<T> pr = pos[i < N - 1 ? i + 1 : i];
+                const Pos<T> qm = bq[i];  // Q_{i-1} of the step's start
+                const T nsp = T(mask_popc(msk[i]));
+                const T Rl[3] = {pl.x, pl.y, pl.z}, Rr[3] = {pr.x, pr.y, pr.z}, Qm[3] = {qm.x, qm.y, qm.z};
+                T F2[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const T fb1 = c.k_b * Q[b][d] - c.k_b * Qm[d];  // the bond part of F
+                    F2[d] = c.k_b * (Rl[d] - Rn[b][d]) + c.k_b * (Rr[d] - Rn[b][d]) + (F[b][d] - fb1) -
+                            c.k_s * nsp * (Rn[b][d] - R[b][d]);
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    Rn[b][d] = R[b][d] + c.hmob * (F[b][d] + F2[d]) + c.amp * nrm[b][d];
+            }
+        } else if constexpr (HEUN) {
             // Stochastic Heun corrector (the second-order stochastic Runge-Kutta
             // step for additive noise): the Euler state above is the predictor;
             // the drift is averaged between the start and the predicted state
